@@ -1,0 +1,392 @@
+"""Benchmark: forward window + discrete adjoint of the windowed LBM-LES.
+
+One step = one pass of the whole hot path on the cylinder-wake workload
+(D2Q9 1024x256, Re 200, |W| = 2000, checkpoints every 100 steps, FP32):
+a forward window of 2000 fused collide-stream launches with sampling and
+checkpoints, the window-end reduction and the consecutive-window test, the
+discrete adjoint over that window (20 segments recomputed from their
+checkpoints, 2000 adjoint launches) and the design gradient.
+
+value = (forward + adjoint) lattice updates / second over all ranks, in MLUPS.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle instead (on this host's cores,
+on a bounded sample of the same workload).  Under torchrun each rank runs an
+independent replica (the path is one GPU per problem).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "forward & adjoint MLUPS and % HBM roofline, FP32/mixed vs FP64 at stated error"
+WORKLOAD = "wake1024x256"
+KERNEL_SRC = os.path.join(ROOT, "paper_2608_19617_b300", "csrc", "kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- roofline --
+
+def bytes_per_lu(case, phase, rs=4):
+    """Algorithmic DRAM bytes per lattice update of one launch (FP32 unless rs=8).
+
+    forward / recompute: read Q populations, write Q, read g: (2Q+1) rs.
+    adjoint: read Q adjoints, Q populations, g; write Q adjoints: (3Q+1) rs;
+    plus 32 B of FP64 (sum, compensation) read+write per design-box node and
+    the objective weight (4 B) per objective-box node at sampling steps.
+    """
+    q, n = case.lattice, case.n
+    if phase in ("forward", "recompute"):
+        return (2 * q + 1) * rs
+    x0, x1, y0, y1, z0, z1 = case.design_box
+    nd = (x1 - x0) * (y1 - y0) * (z1 - z0)
+    x0, x1, y0, y1, z0, z1 = case.obj_box
+    no = (x1 - x0) * (y1 - y0) * (z1 - z0)
+    return (3 * q + 1) * rs + 32.0 * nd / n + 4.0 * no / n / case.sample_every
+
+
+def kernel_hash():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload):
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    for e in t.get("entries", []):
+        if e.get("kernel") == kernel and e.get("workload") == workload and e.get("source_hash") == kernel_hash():
+            return e.get("bytes_per_launch")
+    return None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_sample(case, fwd_steps, seconds_hint=None):
+    """Time the FP64 oracle on a bounded sample of the workload: a window of
+    ``fwd_steps`` steps from a developed-looking start, then its adjoint."""
+    import numpy as np
+    from threadpoolctl import threadpool_limits
+
+    from oracle import lbm as O
+    c = case.replace(window_len=fwd_steps, ckpt_every=fwd_steps, sample_every=1)
+    with threadpool_limits(limits=1):
+        pr = O.Problem(c)
+        p0 = pr.initial_state()
+        t0 = time.perf_counter()
+        _, J, M, traj = pr.run_window(p0)
+        t1 = time.perf_counter()
+        pr.adjoint_window(traj)
+        t2 = time.perf_counter()
+    lus = 2 * fwd_steps * c.n
+    return {"value": lus / (t2 - t0) / 1e6, "fwd_s": t1 - t0, "adj_s": t2 - t1, "seconds": t2 - t0,
+            "lattice_updates": lus, "cores": 1}
+
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args, case, rank, world):
+    if rank != 0:
+        return 0
+    sample_steps = 2
+    for _ in range(args.warmup):
+        oracle_sample(case, sample_steps)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(case, sample_steps)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    value = args.steps * 2 * sample_steps * case.n / secs / 1e6
+    sample = (f"FP64 numpy oracle, one thread: per step a {sample_steps}-step window of the full "
+              f"{case.nx}x{case.ny} lattice plus its adjoint ({2 * sample_steps * case.n} lattice updates)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded inputs shaped like the paper's cylinder wake)",
+        "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "window_len": case.window_len,
+                   "ckpt_every": case.ckpt_every},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU path --
+
+def run_ours(args, case, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2608_19617_b300 import binding as B
+    from paper_2608_19617_b300 import build as bld
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        bld.build()
+    if world > 1:
+        dist.barrier()
+    bld.build()
+    B.lib()
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = B.Solver(case, B.LBM_FP32, stream=stream)
+    n = case.n
+    W, K = case.window_len, case.ckpt_every
+    S = W // K
+    grad_dev = torch.empty(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (126 MB)
+
+    def one_step():
+        sol.step_window()
+        sol.window_converged()
+        sol.adjoint_window()
+        sol.design_gradient(grad_dev)
+
+    # spin-up so that the timed windows see a developed wake
+    sol.advance(4 * W)
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    sol.set_timing(True)
+    sol.get_timing()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xff)
+                ev[k][0].record(stream)
+                one_step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    timing = sol.get_timing()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    lus_step = 2 * W * n
+    value = world * args.steps * lus_step / (ms / 1e3) / 1e6
+
+    # e2e: host design in, host gradient out, through the C ABI, per step.
+    gam_host = torch.from_numpy(case.gamma.reshape(-1).astype(np.float32)).pin_memory()
+    grad_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sol.set_design(gam_host)
+        sol.step_window()
+        sol.window_converged()
+        sol.adjoint_window()
+        sol.design_gradient(grad_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * args.steps * lus_step / e2e_s / 1e6
+
+    if rank != 0:
+        return 0
+
+    pk, pk_kind = peaks()
+    hbm = float(pk["hbm_gbs"])
+    phase_rows = {}
+    for ph in ("forward", "recompute", "adjoint"):
+        t = timing[ph]
+        if t["launches"]:
+            avg_ms = t["ms"] / t["launches"]
+            bpl = bytes_per_lu(case, ph) * n
+            phase_rows[ph] = {"launches": t["launches"], "ms": t["ms"], "avg_launch_us": 1e3 * avg_ms,
+                              "bytes_per_launch": bpl, "gbs": bpl / (avg_ms / 1e3) / 1e9}
+    dom = max(phase_rows, key=lambda p: phase_rows[p]["ms"])
+    kname = {"forward": "fwd_step_kernel", "recompute": "fwd_step_kernel", "adjoint": "adj_step_kernel"}[dom]
+    ach = phase_rows[dom]["gbs"]
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": measured_traffic(kname, case.name), "kernel": kname, "phase": dom,
+            "peak_kind": f"{pk_kind} hbm_gbs (copy)",
+            "bytes_per_lu": bytes_per_lu(case, dom), "phases": phase_rows}
+
+    # Accuracy beside the number: the FP32 window and adjoint against the FP64
+    # GPU path from the same start field.
+    err = None
+    if not args.no_fp64_check:
+        p = sol.get_state()
+        with torch.cuda.stream(stream):
+            ref = B.Solver(case, B.LBM_FP64, stream=stream)
+        ref.set_state(p)
+        sol.set_state(p)
+        J32, _ = sol.step_window()
+        sol.adjoint_window()
+        g32 = sol.design_gradient()
+        J64, _ = ref.step_window()
+        ref.adjoint_window()
+        g64 = ref.design_gradient()
+        cos = float(g32 @ g64 / (np.linalg.norm(g32) * np.linalg.norm(g64)))
+        err = {"J_rel_err_fp32_vs_fp64": abs(J32 - J64) / abs(J64), "grad_cosine_fp32_vs_fp64": cos,
+               "grad_rel_err_fp32_vs_fp64": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+               "window_len": W}
+        ref.close()
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        r = oracle_sample(case, 2)
+        cpu = {"value": r["value"], "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
+               "sample": (f"FP64 numpy oracle, one thread: a 2-step window of the full {case.nx}x{case.ny} "
+                          f"lattice plus its adjoint ({r['lattice_updates']} lattice updates, {r['seconds']:.1f} s)"),
+               "cpu": cpu_model()}
+
+    launches_per_step = W + 1 + (W - S) + W + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded inputs shaped like the paper's cylinder wake)",
+        "config": {"workload": case.name, "lattice": "D2Q9", "nx": case.nx, "ny": case.ny,
+                   "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
+                   "ckpt_format": ["fp32", "fp16", "bf16"][case.ckpt_format], "tau": case.tau,
+                   "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) before every timed step; inside a step the forward "
+                         "lattices (19 MB) stay L2-resident"},
+        "fwd_mlups": 1e-6 * timing["forward"]["lattice_updates"] / (timing["forward"]["ms"] / 1e3),
+        "adj_mlups_incl_recompute": 1e-6 * timing["adjoint"]["lattice_updates"] /
+            ((timing["adjoint"]["ms"] + timing["recompute"]["ms"] + timing["checkpoint"]["ms"]) / 1e3),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "error": err,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_2608_19617_b300 import inputs as I
+    case = I.WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        rc = run_reference(args, case, rank, world)
+        return rc
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, case, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * lbmadj -- windowed regularized lattice-Boltzmann LES and its discrete adjoint
+ * on one NVIDIA B300 (sm_103a).
+ *
+ * The library advances a D2Q9 or D3Q19 lattice with the regularized BGK
+ * collision and Smagorinsky eddy viscosity (Sec. 2.1.2, Eqs. 9-16), partial
+ * bounce-back driven by a design field (Sec. 2.2, Eq. 23), streaming and
+ * boundary rules (Sec. 2.1.3, Eqs. 19-21), one time window at a time.  It
+ * samples a window-averaged objective and a monitored quantity (Sec. 3.1-3.3,
+ * Eqs. 24-27, 42), evaluates the consecutive-window test (Eq. 26), sweeps the
+ * discrete adjoint backward over the last window (Eqs. 30-39) with checkpoint
+ * recompute, and accumulates the design sensitivity (Eq. 40).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an lbm_status; nothing throws across the ABI.
+ *    lbm_last_error() gives a one-line reason for the last failure on the
+ *    calling thread.
+ *  - The caller owns every buffer, including the device workspace passed to
+ *    lbm_create; the library makes no device allocation of its own.  The
+ *    context itself is a small host object freed by lbm_destroy.
+ *  - All device work is enqueued on the CUDA stream given to lbm_create.
+ *    Calls that return host scalars synchronise that stream before returning.
+ *  - Population order: D2Q9 in the paper's order (Eq. 2): c0=(0,0), c1=(1,0),
+ *    c2=(0,1), c3=(-1,0), c4=(0,-1), c5=(1,1), c6=(-1,1), c7=(-1,-1),
+ *    c8=(1,-1).  D3Q19: c0 rest; c1..c6 = +x,-x,+y,-y,+z,-z; c7..c18 =
+ *    (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),
+ *    (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1).
+ *  - Node index i = x + nx*(y + ny*z).  Population arrays are [Q][N] with N
+ *    = nx*ny*nz (structure of arrays, x fastest).
+ *  - Pointers documented "host or device" may point to either; the library
+ *    tells them apart through unified addressing.
+ *  - The design field gamma is the solid fraction (1 = solid); the paper's
+ *    design variable is phi = 1 - gamma.  Gradients returned are dJ/dgamma.
+ */
+#ifndef LBMADJ_H
+#define LBMADJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,        /* invalid argument or configuration (nothing changed) */
+  LBM_ERR_WORKSPACE = 2,  /* workspace pointer misaligned or too small           */
+  LBM_ERR_CUDA = 3,       /* a CUDA runtime call failed                          */
+  LBM_ERR_STATE = 4,      /* call out of order (e.g. adjoint before a window)    */
+  LBM_ERR_NONFINITE = 5,  /* a density <= 0 or a non-finite value was produced   */
+  LBM_NOT_CONVERGED = 6   /* reserved for drivers that bound the window loop     */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
+enum { LBM_FP32 = 0, LBM_FP64 = 1 };
+
+/* Node classes.  Only nodes on the domain faces may be non-FLUID.
+ *  WALL: on-node bounce-back; an unknown population takes the value of its
+ *        opposite (Eq. 19); a link whose opposite is unknown too (a corner)
+ *        takes its rest weight w_a.
+ *  INLET: velocity inlet on the x=0 face with x-velocity inlet_u[z][y]:
+ *        Zou-He (Eq. 20) for D2Q9; moving-wall bounce-back for D3Q19.
+ *  OUTLET_PRESSURE: Zou-He pressure outlet (Eq. 21) on the x=nx-1 face,
+ *        density rho_out; D2Q9 only.
+ *  OUTLET_ZEROGRAD: unknown populations copied from the neighbour along the
+ *        inward x normal, on the x=0 or x=nx-1 face. */
+enum { LBM_FLUID = 0, LBM_WALL = 1, LBM_INLET = 2, LBM_OUTLET_PRESSURE = 3, LBM_OUTLET_ZEROGRAD = 4 };
+
+/* Instantaneous objective j(t) = sum_i w_i psi_i (window mean: Eq. 27, 42).
+ *  DISSIPATION:   psi = (tau_eff - 1/2) Pi:Pi / (2 rho cs^2 tau_eff^2)
+ *  VELOCITY_DEV:  psi = |u - objective_uref|^2
+ *  PRESSURE:      psi = cs^2 rho (signed weights give a pressure drop, Eq. 47)
+ *  DRAG:          psi = sum_a c_xa F_a with F from Eq. 23 (Eq. 44) */
+enum { LBM_OBJ_DISSIPATION = 0, LBM_OBJ_VELOCITY_DEV = 1, LBM_OBJ_PRESSURE = 2, LBM_OBJ_DRAG = 3 };
+
+/* Monitored quantity of the window test: the drag coefficient of Eq. 25,
+ * sum_i sum_a c_xa F_a / (rho_out monitor_u^2 monitor_l / 2), or j itself. */
+enum { LBM_MON_DRAG = 0, LBM_MON_OBJECTIVE = 1 };
+
+/* Checkpoint storage for the adjoint's recompute: the working precision, or
+ * the deviation from equilibrium in FP16/BF16 with one power-of-two scale per
+ * block of nodes plus FP32 density and momentum (lossy; FP32 solver only). */
+enum { LBM_CKPT_NATIVE = 0, LBM_CKPT_FP16 = 1, LBM_CKPT_BF16 = 2 };
+
+typedef struct {
+  int32_t lattice;          /* LBM_D2Q9 or LBM_D3Q19                                  */
+  int32_t nx, ny, nz;       /* lattice size; nz = 1 for D2Q9                          */
+  int32_t precision;        /* LBM_FP32 or LBM_FP64 (populations and adjoint)          */
+  int32_t periodic[3];      /* 1 = periodic along x / y / z                           */
+  double tau;               /* molecular relaxation time, nu = (tau - 1/2)/3 (Eq. 8)  */
+  double cs_smag;           /* Smagorinsky constant C_s, filter width 1 (Eq. 9)       */
+  double q_interp;          /* interpolation parameter of g(phi) (Sec. 2.2)           */
+  double g_max;             /* g at phi = 0; the paper's value is 0.5                 */
+  double rho_out;           /* outlet and reference density rho_0                     */
+  int32_t objective_kind;   /* LBM_OBJ_*                                              */
+  int32_t monitor_kind;     /* LBM_MON_*                                              */
+  double objective_uref[3]; /* reference velocity of LBM_OBJ_VELOCITY_DEV              */
+  double monitor_u;         /* reference velocity of the drag coefficient             */
+  double monitor_l;         /* reference length of the drag coefficient               */
+  int32_t window_len;       /* |W|, steps per window                                  */
+  int32_t sample_every;     /* Delta W; must divide window_len                        */
+  double conv_tol;          /* epsilon of Eq. 26                                      */
+  int32_t ckpt_every;       /* K; must divide window_len                              */
+  int32_t ckpt_format;      /* LBM_CKPT_*                                             */
+  int32_t obj_box[6];       /* x0,x1,y0,y1,z0,z1 (half-open): weights read only here  */
+  int32_t design_box[6];    /* x0,x1,y0,y1,z0,z1 (half-open): gradient nonzero only here */
+} lbm_config;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Phase timings measured with CUDA events on the context's stream when timing
+ * is enabled: milliseconds and launch counts per phase since the last reset.
+ * Phase 0: forward steps of lbm_step_window; 1: recompute steps of
+ * lbm_adjoint_window; 2: adjoint steps; 3: checkpoint copies/encodes/decodes. */
+#define LBM_NUM_PHASES 4
+typedef struct {
+  double ms[LBM_NUM_PHASES];
+  int64_t launches[LBM_NUM_PHASES];
+  int64_t lattice_updates[LBM_NUM_PHASES];
+} lbm_timing;
+
+/* Bytes of device workspace lbm_create needs for cfg (validates cfg).
+ * Returns LBM_ERR_ARG for an invalid configuration. */
+lbm_status lbm_workspace_size(const lbm_config* cfg, size_t* bytes);
+
+/* Create a solver.  Inputs are copied; the caller may free them afterwards.
+ *   node_class        host, uint8 [N], LBM_FLUID..LBM_OUTLET_ZEROGRAD
+ *   design_gamma      host or device, float [N], values in [0, 1]
+ *   objective_weights host or device, float [N] (read inside obj_box only) or NULL = 0
+ *   inlet_u           host or device, float [nz][ny] x-velocity on the x=0 face, or NULL = 0
+ *   workspace         device, >= lbm_workspace_size bytes, 256-byte aligned, owned by the
+ *                     caller and kept alive until lbm_destroy
+ *   stream            cudaStream_t to enqueue on (NULL = legacy default stream)
+ * The carried populations start at rest equilibrium (rho = 1, u = 0; Eq. 18).
+ * Errors: LBM_ERR_ARG (bad cfg, classes or values), LBM_ERR_WORKSPACE, LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const float* design_gamma,
+                      const float* objective_weights, const float* inlet_u, void* workspace,
+                      size_t workspace_bytes, void* stream, lbm_ctx** out);
+
+/* Run one window of |W| steps (Alg. 1 inner loop, Eqs. 24, 27, 42) and store
+ * its checkpoints.  Returns the window means of the objective and of the
+ * monitored quantity.  Synchronises the stream.
+ * Errors: LBM_ERR_NONFINITE (the window produced rho <= 0 or NaN/Inf; the
+ * window is not recorded), LBM_ERR_CUDA. */
+lbm_status lbm_step_window(lbm_ctx* ctx, double* J_window, double* monitor_window);
+
+/* Consecutive-window test of Eq. 26 between the last two windows:
+ * ratio = |(M_i - M_{i-1}) / M_i| (absolute difference when |M_i| < 1e-30),
+ * converged = ratio < conv_tol.  Before two windows: converged = 0,
+ * ratio = +inf.  Host only, no GPU work. */
+lbm_status lbm_window_converged(lbm_ctx* ctx, int* converged, double* ratio);
+
+/* Discrete adjoint over the last completed window (Alg. 2 reverse loop,
+ * Eqs. 35-39), recomputing each segment of K steps from its checkpoint, and
+ * the design sensitivity (Eq. 40) accumulated in FP64 with compensated
+ * summation.  Returns that window's objective J_eff (Eq. 27).  Synchronises.
+ * Errors: LBM_ERR_STATE if no window has completed since the last
+ * lbm_create / lbm_set_state / lbm_set_design. */
+lbm_status lbm_adjoint_window(lbm_ctx* ctx, double* J_eff);
+
+/* dJ_eff/dgamma of the last adjoint window into grad (host or device, FP64
+ * [N]); zero outside design_box.  n must equal N.
+ * Errors: LBM_ERR_STATE before lbm_adjoint_window, LBM_ERR_ARG for n != N. */
+lbm_status lbm_design_gradient(lbm_ctx* ctx, double* grad, size_t n);
+
+/* Replace the design field (host or device, float [N]); geometry unchanged.
+ * Invalidates the recorded window and gradient. */
+lbm_status lbm_set_design(lbm_ctx* ctx, const float* design_gamma);
+
+/* Read / write the carried post-collision populations p (FP64, [Q][N], host
+ * or device, n = Q*N).  lbm_set_state invalidates the recorded window. */
+lbm_status lbm_get_state(lbm_ctx* ctx, double* f, size_t n);
+lbm_status lbm_set_state(lbm_ctx* ctx, const double* f, size_t n);
+
+/* dJ_eff / d p^{n0-1}: the adjoint of the field the last adjoint window
+ * started from (FP64, [Q][N], host or device, n = Q*N). */
+lbm_status lbm_get_adjoint_state(lbm_ctx* ctx, double* a, size_t n);
+
+/* Advance nsteps steps without sampling or checkpoints (spin-up). */
+lbm_status lbm_advance(lbm_ctx* ctx, int32_t nsteps);
+
+/* Enable (1) / disable (0) phase timing; lbm_get_timing copies and resets. */
+lbm_status lbm_set_timing(lbm_ctx* ctx, int32_t enable);
+lbm_status lbm_get_timing(lbm_ctx* ctx, lbm_timing* out);
+
+/* Total steps advanced and windows completed since lbm_create. */
+lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);
+
+const char* lbm_status_string(lbm_status s);
+const char* lbm_last_error(void);
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMADJ_H */

@@ -1,0 +1,805 @@
+// Device code of the windowed regularized LBM-LES and its discrete adjoint.
+//
+// Storage: populations are kept shifted by their rest weights, p~_a = p_a - w_a,
+// in structure-of-arrays layout [Q][N] (x fastest).  Near the rest state the
+// shifted values are small, so FP32 keeps the non-equilibrium part (which
+// drives the collision at tau ~ 0.5) to full relative precision.  All
+// formulas below are the paper's, rewritten in the shifted variables; the
+// shift cancels exactly wherever it enters (w_a = w_abar, sum w c = 0,
+// sum w c c = cs^2 I).
+//
+// One thread owns one lattice node.  A forward step pulls p^{n-1} from the
+// upstream neighbours (streaming, Eq. 7), completes the boundary populations
+// (Eqs. 19-21), collides (Eqs. 12-16), blends (Eq. 23) and stores p^n at its
+// own node: 4Q bytes read + 4Q bytes written + 4 bytes of g per node in FP32.
+// An adjoint step pulls the adjoint of p^n from the downstream neighbours
+// (Eq. 36), recomputes f^n from p^{n-1}, applies the transposed local
+// Jacobian in moment space (Eq. 35) and the transposed boundary rule
+// (Eqs. 37-39), and stores the result at its own node.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+enum : uint8_t { FLUID = 0, WALL = 1, INLET = 2, OUTLET_P = 3, OUTLET_ZG = 4 };
+enum { OBJ_DISS = 0, OBJ_VEL = 1, OBJ_PRES = 2, OBJ_DRAG = 3 };
+enum { MON_DRAG = 0, MON_OBJ = 1 };
+
+constexpr int kBlock = 128;   // threads per block (one row segment of 128 nodes)
+
+struct Geo {
+  int nx, ny, nz;
+  int px, py, pz;             // periodic flags
+  long long n;                // nx*ny*nz
+  long long sy, sz;           // strides of y and z
+};
+
+template <class R>
+struct Phys {
+  R tau;       // molecular relaxation time
+  R c2;        // (C_s * filter width)^2
+  R rho_out;   // outlet density
+};
+
+// Objective description (sampling instants only).
+template <class R>
+struct Obj {
+  int kind;
+  int mon;               // monitored quantity
+  R uref[3];
+  int box[6];            // weights read only inside
+  R ws;                  // sampling weight dW/|W| (adjoint source scale)
+  double mon_scale;      // 1 / (rho0 U^2 L / 2) for the drag coefficient
+  double jconst;         // constant part of j (cs^2 * sum of weights for PRESSURE)
+};
+
+// Window accumulators (FP64, compensated) and the window-end results.
+struct WindowAcc {
+  double jsum, jcomp, msum, mcomp;
+  long long count;
+  double jmean, mmean, mprev, ratio;
+  int has_prev, converged, nonfinite, pad;
+};
+
+template <class T>
+__device__ __forceinline__ T cs2() { return T(1.0 / 3.0); }
+
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+  s = t;
+}
+
+// Neighbour (x+dx, y+dy, z+dz) with periodic wrap; false if outside.
+__device__ __forceinline__ bool neighbour(const Geo& g, int x, int y, int z, int dx, int dy, int dz,
+                                          long long& j) {
+  int X = x + dx, Y = y + dy, Z = z + dz;
+  if (X < 0 || X >= g.nx) { if (!g.px) return false; X = (X + g.nx) % g.nx; }
+  if (Y < 0 || Y >= g.ny) { if (!g.py) return false; Y = (Y + g.ny) % g.ny; }
+  if (Z < 0 || Z >= g.nz) { if (!g.pz) return false; Z = (Z + g.nz) % g.nz; }
+  j = X + Y * g.sy + Z * g.sz;
+  return true;
+}
+
+template <class L>
+__device__ __forceinline__ bool on_face(const Geo& g, int x, int y, int z) {
+  bool f = (x == 0) | (x == g.nx - 1) | (y == 0) | (y == g.ny - 1);
+  if (L::D == 3) f |= (z == 0) | (z == g.nz - 1);
+  return f;
+}
+
+template <class L>
+__device__ __forceinline__ long long offset(const Geo& g, int a) {
+  return L::cx(a) + L::cy(a) * g.sy + L::cz(a) * g.sz;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming with boundary completion: f^n at node (x,y,z) from p^{n-1}.
+// ---------------------------------------------------------------------------
+template <class L, class R>
+__device__ __forceinline__ void gather(const R* __restrict__ P, const Geo& g, int x, int y, int z,
+                                       long long i, bool face, uint8_t cls, R u0, R rho_out,
+                                       R (&f)[L::Q], unsigned& unk) {
+  unk = 0;
+  if (!face) {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) f[a] = P[a * g.n + i - offset<L>(g, a)];
+    return;
+  }
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) {
+    long long j;
+    if (neighbour(g, x, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j)) {
+      f[a] = P[a * g.n + j];
+    } else {
+      f[a] = R(0);
+      unk |= 1u << a;
+    }
+  }
+  if (!unk) return;
+  if (cls == WALL) {
+    // Eq. 19: an unknown population takes its opposite's value; a link whose
+    // opposite is unknown too stays at its rest weight (shifted value 0).
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a)
+      if (unk & (1u << a)) f[a] = (unk & (1u << L::opp(a))) ? R(0) : f[L::opp(a)];
+  } else if (cls == INLET) {
+    if (L::Q == 9) {
+      // Zou-He velocity inlet, Eq. 20, in shifted form (w1=w3, w5=w7, w2=w4).
+      const R s = f[0] + f[2] + f[4] + R(2) * (f[3] + f[6] + f[7]);
+      const R rho = (R(1) + s) / (R(1) - u0);
+      const R ru = rho * u0;
+      f[1] = f[3] + R(2.0 / 3.0) * ru;
+      f[5] = f[7] + R(0.5) * (f[4] - f[2]) + ru * R(1.0 / 6.0);
+      f[8] = f[6] + R(0.5) * (f[2] - f[4]) + ru * R(1.0 / 6.0);
+    } else {
+      // Moving-wall bounce-back with rho0 = 1: f_a = f_abar + 2 w_a c_a.u / cs^2.
+#pragma unroll
+      for (int a = 0; a < L::Q; ++a)
+        if (unk & (1u << a)) f[a] = f[L::opp(a)] + R(6.0 * L::w(a) * L::cx(a)) * u0;
+    }
+  } else if (cls == OUTLET_P) {
+    // Zou-He pressure outlet, Eq. 21 (D2Q9): u = (1 + s)/rho0 - 1 in shifted form.
+    const R s = f[0] + f[2] + f[4] + R(2) * (f[1] + f[5] + f[8]);
+    const R ux = (R(1) + s) / rho_out - R(1);
+    const R ru = rho_out * ux;
+    f[3] = f[1] - R(2.0 / 3.0) * ru;
+    f[6] = f[8] + R(0.5) * (f[4] - f[2]) - ru * R(1.0 / 6.0);
+    f[7] = f[5] + R(0.5) * (f[2] - f[4]) - ru * R(1.0 / 6.0);
+  } else if (cls == OUTLET_ZG) {
+    // Unknown f_a(i) = f_a(i + n_in) after streaming = p_a(i + n_in - c_a).
+    const int xn = (x == g.nx - 1) ? x - 1 : x + 1;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+      if (unk & (1u << a)) {
+        long long j = 0;
+        neighbour(g, xn, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j);   // inside (validated on the host)
+        f[a] = P[a * g.n + j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Moments and the regularized LES collision (Eqs. 5, 12-16), shifted form.
+// ---------------------------------------------------------------------------
+template <class L, class R>
+struct Mom {
+  R rt, rho, inv;          // rho - 1, rho, 1/rho
+  R m[3], u[3];            // momentum, velocity
+  R pi[6];                 // Pi_xx, Pi_yy, Pi_zz, Pi_xy, Pi_xz, Pi_yz  (Eq. 13)
+  R pp;                    // Pi:Pi
+  R pn;                    // |Pi| = sqrt(2 Pi:Pi)
+  R s;                     // sqrt(tau^2 + 2 C^2 |Pi| / (rho cs^4))
+  R te, om;                // tau_eff (Eq. 14), 1 - 1/tau_eff
+};
+
+template <class L, class R>
+__device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<L, R>& M) {
+  R rt = 0, mx = 0, my = 0, mz = 0, xx = 0, yy = 0, zz = 0, xy = 0, xz = 0, yz = 0;
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) {
+    const R v = f[a];
+    rt += v;
+    if (L::cx(a)) mx += L::cx(a) * v;
+    if (L::cy(a)) my += L::cy(a) * v;
+    if (L::cz(a)) mz += L::cz(a) * v;
+    if (L::cx(a)) xx += v;
+    if (L::cy(a)) yy += v;
+    if (L::cz(a)) zz += v;
+    if (L::cx(a) * L::cy(a)) xy += (L::cx(a) * L::cy(a)) * v;
+    if (L::cx(a) * L::cz(a)) xz += (L::cx(a) * L::cz(a)) * v;
+    if (L::cy(a) * L::cz(a)) yz += (L::cy(a) * L::cz(a)) * v;
+  }
+  M.rt = rt;
+  M.rho = R(1) + rt;
+  M.inv = R(1) / M.rho;
+  M.m[0] = mx; M.m[1] = my; M.m[2] = mz;
+  M.u[0] = mx * M.inv; M.u[1] = my * M.inv; M.u[2] = mz * M.inv;
+  // Pi = M2 - rho cs^2 I - m m^T / rho; with shifted moments M2~ = M2 - cs^2 I.
+  const R c = cs2<R>();
+  M.pi[0] = xx - rt * c - mx * M.u[0];
+  M.pi[1] = yy - rt * c - my * M.u[1];
+  M.pi[2] = (L::D == 3) ? zz - rt * c - mz * M.u[2] : R(0);
+  M.pi[3] = xy - mx * M.u[1];
+  M.pi[4] = (L::D == 3) ? xz - mx * M.u[2] : R(0);
+  M.pi[5] = (L::D == 3) ? yz - my * M.u[2] : R(0);
+  M.pp = M.pi[0] * M.pi[0] + M.pi[1] * M.pi[1] + M.pi[2] * M.pi[2] +
+         R(2) * (M.pi[3] * M.pi[3] + M.pi[4] * M.pi[4] + M.pi[5] * M.pi[5]);
+  M.pn = sqrt(R(2) * M.pp);
+  // Eq. 14: 2 C^2 |Pi| / (rho cs^4) = 18 C^2 |Pi| / rho.
+  M.s = sqrt(ph.tau * ph.tau + R(18) * ph.c2 * M.pn * M.inv);
+  M.te = R(0.5) * (ph.tau + M.s);
+  M.om = R(1) - R(1) / M.te;
+}
+
+// h~_a = f^eq_a - w_a + (1 - 1/tau_eff) w_a/(2 cs^4) (c_a c_a - cs^2 I) : Pi   (Eq. 16)
+template <class L, class R>
+__device__ __forceinline__ R regularized(const Mom<L, R>& M, int a) {
+  const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+  const R cu = cx * M.u[0] + cy * M.u[1] + cz * M.u[2];
+  const R uu = M.u[0] * M.u[0] + M.u[1] * M.u[1] + M.u[2] * M.u[2];
+  const R w = R(L::w(a));
+  const R feq = w * (M.rt + M.rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+  const R tr = M.pi[0] + M.pi[1] + M.pi[2];
+  const R qpi = R(cx * cx) * M.pi[0] + R(cy * cy) * M.pi[1] + R(cz * cz) * M.pi[2] +
+                R(2 * cx * cy) * M.pi[3] + R(2 * cx * cz) * M.pi[4] + R(2 * cy * cz) * M.pi[5] -
+                cs2<R>() * tr;
+  return feq + M.om * R(4.5) * w * qpi;
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of two FP64 values; result in thread 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[kBlock / 32], sb[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+  __syncthreads();
+  if (warp == 0) {
+    a = lane < kBlock / 32 ? sa[lane] : 0.0;
+    b = lane < kBlock / 32 ? sb[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+  __syncthreads();
+}
+
+// Per-block partials, then the last block to finish sums them in a fixed
+// order (deterministic) with compensation and adds the sample to the window.
+__device__ __forceinline__ void sample_commit(double bj, double bm, double* partials,
+                                              unsigned* counter, WindowAcc* acc, double jconst,
+                                              double mon_scale, int mon_kind) {
+  __shared__ bool last;
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (threadIdx.x == 0) {
+    partials[2 * bid] = bj;
+    partials[2 * bid + 1] = bm;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == nb - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sj = 0, cj = 0, sm = 0, cm = 0;
+  const volatile double* vp = partials;
+  for (unsigned k = threadIdx.x; k < nb; k += blockDim.x) {
+    neumaier(sj, cj, vp[2 * k]);
+    neumaier(sm, cm, vp[2 * k + 1]);
+  }
+  double tj = sj + cj, tm = sm + cm;
+  block_sum2(tj, tm);
+  if (threadIdx.x == 0) {
+    const double j = tj + jconst;
+    const double m = mon_kind == MON_DRAG ? tm * mon_scale : j;
+    neumaier(acc->jsum, acc->jcomp, j);
+    neumaier(acc->msum, acc->mcomp, m);
+    acc->count += 1;
+    *counter = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward step.
+// ---------------------------------------------------------------------------
+template <class R>
+struct FwdArgs {
+  const R* __restrict__ src;     // p^{n-1}
+  R* __restrict__ dst;           // p^n
+  const R* __restrict__ gfield;  // g(phi) per node
+  const uint8_t* __restrict__ cls;
+  const float* __restrict__ uin; // [nz][ny]
+  const float* __restrict__ wobj;
+  Geo geo;
+  Phys<R> ph;
+  Obj<R> obj;
+  int sample;                    // 1 at a sampling instant
+  double* partials;
+  unsigned* counter;
+  WindowAcc* acc;
+  int* nonfinite;
+};
+
+template <class L, class R>
+__device__ __forceinline__ R local_objective(const Mom<L, R>& M, const Obj<R>& ob, R gi) {
+  switch (ob.kind) {
+    case OBJ_DISS: return R(1.5) * (M.te - R(0.5)) * M.pp * M.inv / (M.te * M.te);
+    case OBJ_VEL: {
+      const R dx = M.u[0] - ob.uref[0], dy = M.u[1] - ob.uref[1], dz = M.u[2] - ob.uref[2];
+      return dx * dx + dy * dy + (L::D == 3 ? dz * dz : R(0));
+    }
+    case OBJ_PRES: return cs2<R>() * M.rt;     // constant cs^2 sum(w) added once per sample
+    default: return R(-2) * gi * M.m[0];       // sum_a c_xa F_a = -2 g m_x
+  }
+}
+
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) fwd_step_kernel(FwdArgs<R> A) {
+  const Geo& g = A.geo;
+  const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  const bool alive = x < g.nx;
+  double bj = 0.0, bm = 0.0;
+  if (alive) {
+    const long long i = x + y * g.sy + z * g.sz;
+    const bool face = on_face<L>(g, x, y, z);
+    const uint8_t cls = face ? A.cls[i] : uint8_t(FLUID);
+    const R u0 = (face && cls == INLET) ? R(A.uin[y + g.ny * z]) : R(0);
+    R f[L::Q];
+    unsigned unk;
+    gather<L, R>(A.src, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f, unk);
+    Mom<L, R> M;
+    moments<L, R>(f, A.ph, M);
+    if (!(M.rho > R(0)) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
+    const R gi = A.gfield[i];
+    R h[L::Q];
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) h[a] = regularized<L, R>(M, a);
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = h[a] + gi * (h[L::opp(a)] - h[a]);   // Eq. 23
+    if (A.sample) {
+      const int* b = A.obj.box;
+      if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
+        const R w = R(A.wobj[i]);
+        if (w != R(0)) bj = double(w * local_objective<L, R>(M, A.obj, gi));
+      }
+      if (A.obj.mon == MON_DRAG) bm = double(R(-2) * gi * M.m[0]);
+    }
+  }
+  if (A.sample) {   // uniform across the grid
+    block_sum2(bj, bm);
+    sample_commit(bj, bm, A.partials, A.counter, A.acc, A.obj.jconst, A.obj.mon_scale, A.obj.mon);
+  }
+}
+
+// Window end: means (Eq. 42), consecutive-window ratio (Eq. 26), reset.
+__global__ void window_end_kernel(WindowAcc* acc, double tol, int* nonfinite) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double n = double(acc->count > 0 ? acc->count : 1);
+  const double jm = (acc->jsum + acc->jcomp) / n;
+  const double mm = (acc->msum + acc->mcomp) / n;
+  if (acc->has_prev) {
+    const double d = fabs(mm - acc->mprev);
+    acc->ratio = fabs(mm) < 1e-30 ? d : d / fabs(mm);
+    acc->converged = acc->ratio < tol;
+  } else {
+    acc->ratio = __longlong_as_double(0x7ff0000000000000LL);
+    acc->converged = 0;
+  }
+  acc->jmean = jm;
+  acc->mmean = mm;
+  acc->mprev = mm;
+  acc->has_prev = 1;
+  acc->nonfinite = *nonfinite;
+  acc->jsum = acc->jcomp = acc->msum = acc->mcomp = 0.0;
+  acc->count = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint step (Eqs. 35-39), moment-space form of the transposed Jacobian.
+//
+// The collision h(f) depends on f only through rho, m and M2 = sum c c f, so
+// (dh/df)^T v = d/drho + c_a . d/dm + c_a c_a : d/dM2 of psi = sum_b v_b h_b.
+// The gradients of psi with respect to those moments are obtained by reverse
+// differentiation of Eqs. 3, 13, 14, 16 (and of the objective), O(Q) work.
+// ---------------------------------------------------------------------------
+template <class R>
+struct AdjArgs {
+  const R* __restrict__ bnext;   // adjoint of p^n's consumers: b^{n+1} after the boundary transpose
+  const R* __restrict__ pprev;   // p^{n-1}
+  R* __restrict__ bout;          // b^n after the boundary transpose
+  const R* __restrict__ gfield;
+  const uint8_t* __restrict__ cls;
+  const float* __restrict__ uin;
+  const float* __restrict__ wobj;
+  double2* __restrict__ gacc;    // per-node (sum, compensation) of the sensitivity
+  Geo geo;
+  Phys<R> ph;
+  Obj<R> obj;
+  int sample;
+  int terminal;                  // 1: b^{n+1} = 0 (last step of the window)
+  int dbox[6];                   // design box
+};
+
+// Transposed boundary completion at node i (in place on b).
+template <class L, class R>
+__device__ __forceinline__ void bc_transpose(R (&b)[L::Q], unsigned unk, uint8_t cls, R u0, R rho_out) {
+  if (!unk) return;
+  if (cls == WALL) {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a)
+      if ((unk & (1u << a)) && !(unk & (1u << L::opp(a)))) b[L::opp(a)] += b[a];
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a)
+      if (unk & (1u << a)) b[a] = R(0);
+  } else if (cls == INLET) {
+    if (L::Q == 9) {
+      // Transpose of Eq. 20: the coefficients of Eq. 38, chi = u0/(1-u0).
+      const R chi = u0 / (R(1) - u0);
+      const R t = chi * (R(2.0 / 3.0) * b[1] + R(1.0 / 6.0) * (b[5] + b[8]));
+      const R b1 = b[1], b5 = b[5], b8 = b[8];
+      b[0] += t;
+      b[2] += t + R(0.5) * (b8 - b5);
+      b[4] += t + R(0.5) * (b5 - b8);
+      b[3] += R(2) * t + b1;
+      b[6] += R(2) * t + b8;
+      b[7] += R(2) * t + b5;
+      b[1] = b[5] = b[8] = R(0);
+    } else {
+#pragma unroll
+      for (int a = 0; a < L::Q; ++a)
+        if (unk & (1u << a)) { b[L::opp(a)] += b[a]; b[a] = R(0); }
+    }
+  } else if (cls == OUTLET_P) {
+    // Transpose of Eq. 21: the coefficients of Eq. 39.
+    const R t = R(-2.0 / 3.0) * b[3] - R(1.0 / 6.0) * (b[6] + b[7]);
+    const R b3 = b[3], b6 = b[6], b7 = b[7];
+    b[0] += t;
+    b[2] += t + R(0.5) * (b7 - b6);
+    b[4] += t + R(0.5) * (b6 - b7);
+    b[1] += R(2) * t + b3;
+    b[8] += R(2) * t + b6;
+    b[5] += R(2) * t + b7;
+    b[3] = b[6] = b[7] = R(0);
+  }
+  // OUTLET_ZG: the unknown entries keep b_a(i); the node they were copied
+  // from pulls them (see adj_step_kernel).
+}
+
+// a_k(i) = b_k(i + c_k): adjoint streaming (Eq. 36), pulled from downstream,
+// plus the transposed zero-gradient copies.  b == nullptr means b = 0.
+template <class L, class R>
+__device__ __forceinline__ void pull_adjoint(const R* __restrict__ b, const uint8_t* __restrict__ cls,
+                                             const Geo& g, int x, int y, int z, long long i, bool face,
+                                             R (&a)[L::Q]) {
+  if (b == nullptr) {
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) a[k] = R(0);
+  } else if (!face) {
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) a[k] = b[k * g.n + i + offset<L>(g, k)];
+  } else {
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) {
+      long long j;
+      a[k] = neighbour(g, x, y, z, L::cx(k), L::cy(k), L::cz(k), j) ? b[k * g.n + j] : R(0);
+    }
+    // A zero-gradient outlet node j copied p_k(i) into its unknown f_k(j),
+    // j = i + c_k - n_in; pull those adjoints back.
+    if (x == g.nx - 1 || x == 0) {
+      const int sx = (x == g.nx - 1) ? -1 : 1;   // c_kx of the directions unknown on this face
+#pragma unroll
+      for (int k = 0; k < L::Q; ++k) {
+        if (L::cx(k) != sx) continue;
+        long long j;
+        if (neighbour(g, x, y, z, 0, L::cy(k), L::cz(k), j) && cls[j] == OUTLET_ZG) a[k] += b[k * g.n + j];
+      }
+    }
+  }
+}
+
+// Adjoint of the window's start field: a = S^T b (no collision).
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) adj_pull_kernel(const R* __restrict__ b, const uint8_t* __restrict__ cls,
+                                                          R* __restrict__ out, Geo g) {
+  const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long i = x + y * g.sy + z * g.sz;
+  R a[L::Q];
+  pull_adjoint<L, R>(b, cls, g, x, y, z, i, on_face<L>(g, x, y, z), a);
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) out[k * g.n + i] = a[k];
+}
+
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
+  const Geo& g = A.geo;
+  const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  if (x >= g.nx) return;
+  const long long i = x + y * g.sy + z * g.sz;
+  const bool face = on_face<L>(g, x, y, z);
+  const uint8_t cls = face ? A.cls[i] : uint8_t(FLUID);
+  const R u0 = (face && cls == INLET) ? R(A.uin[y + g.ny * z]) : R(0);
+
+  R a[L::Q];
+  pull_adjoint<L, R>(A.terminal ? nullptr : A.bnext, A.cls, g, x, y, z, i, face, a);
+
+  R f[L::Q];
+  unsigned unk;
+  gather<L, R>(A.pprev, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f, unk);
+  Mom<L, R> M;
+  moments<L, R>(f, A.ph, M);
+  const R gi = A.gfield[i];
+
+  // Sensitivity term of Eq. 40: sum_b a_b (h_bbar - h_b), times g'(phi) later.
+  R gt = 0;
+  {
+    R h[L::Q];
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) h[k] = regularized<L, R>(M, k);
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) gt += a[k] * (h[L::opp(k)] - h[k]);
+  }
+
+  // v = (d p / d h)^T a  (transpose of the blend of Eq. 23)
+  R V0 = 0, V1[3] = {0, 0, 0}, V2[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) {
+    const R v = R(L::w(k)) * (a[k] + gi * (a[L::opp(k)] - a[k]));
+    const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
+    V0 += v;
+    if (cx) V1[0] += cx * v;
+    if (cy) V1[1] += cy * v;
+    if (cz) V1[2] += cz * v;
+    if (cx) V2[0] += v;
+    if (cy) V2[1] += v;
+    if (cz) V2[2] += v;
+    if (cx * cy) V2[3] += (cx * cy) * v;
+    if (cx * cz) V2[4] += (cx * cz) * v;
+    if (cy * cz) V2[5] += (cy * cz) * v;
+  }
+  const R* u = M.u;
+  const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  // V2 u (symmetric V2)
+  const R V2u0 = V2[0] * u[0] + V2[3] * u[1] + V2[4] * u[2];
+  const R V2u1 = V2[3] * u[0] + V2[1] * u[1] + V2[5] * u[2];
+  const R V2u2 = V2[4] * u[0] + V2[5] * u[1] + V2[2] * u[2];
+  const R uV2u = u[0] * V2u0 + u[1] * V2u1 + u[2] * V2u2;
+  // psi_eq = rho E(u):  E = V0 + 3 V1.u + 4.5 u.V2.u - 1.5 V0 u.u   (Eq. 3)
+  const R E = V0 + R(3) * (V1[0] * u[0] + V1[1] * u[1] + V1[2] * u[2]) + R(4.5) * uV2u - R(1.5) * V0 * uu;
+  R cu[3];   // d psi / d u at fixed rho
+  cu[0] = M.rho * (R(3) * V1[0] + R(9) * V2u0 - R(3) * V0 * u[0]);
+  cu[1] = M.rho * (R(3) * V1[1] + R(9) * V2u1 - R(3) * V0 * u[1]);
+  cu[2] = M.rho * (R(3) * V1[2] + R(9) * V2u2 - R(3) * V0 * u[2]);
+  R crho = E;          // d psi / d rho at fixed u, Pi, tau_eff
+  R cm[3] = {0, 0, 0}; // d psi / d m directly
+  // psi_neq = om * 4.5 R:Pi with R = V2 - cs^2 V0 I   (Eq. 16)
+  const R c = cs2<R>();
+  R Rm[6] = {V2[0] - c * V0, V2[1] - c * V0, (L::D == 3 ? V2[2] - c * V0 : R(0)), V2[3], V2[4], V2[5]};
+  const R RP = R(4.5) * (Rm[0] * M.pi[0] + Rm[1] * M.pi[1] + Rm[2] * M.pi[2] +
+                         R(2) * (Rm[3] * M.pi[3] + Rm[4] * M.pi[4] + Rm[5] * M.pi[5]));
+  R ctau = RP / (M.te * M.te);   // d psi / d tau_eff through om = 1 - 1/tau_eff
+  R cpi[6];                      // d psi / d Pi_pq (full symmetric matrix entries)
+#pragma unroll
+  for (int k = 0; k < 6; ++k) cpi[k] = M.om * R(4.5) * Rm[k];
+
+  if (A.sample) {
+    const int* bx = A.obj.box;
+    if (x >= bx[0] && x < bx[1] && y >= bx[2] && y < bx[3] && z >= bx[4] && z < bx[5]) {
+      const R ws = R(A.wobj[i]) * A.obj.ws;
+      if (ws != R(0)) {
+        switch (A.obj.kind) {
+          case OBJ_DISS: {
+            // psi = 1.5 (te - 1/2) Pi:Pi / (rho te^2)
+            const R k0 = R(1.5) * M.inv / (M.te * M.te);
+            const R val = k0 * (M.te - R(0.5)) * M.pp;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) cpi[k] += ws * R(2) * k0 * (M.te - R(0.5)) * M.pi[k];
+            ctau += ws * R(1.5) * M.pp * M.inv * (R(1) - M.te) / (M.te * M.te * M.te);
+            crho += -ws * val * M.inv;
+            break;
+          }
+          case OBJ_VEL: {
+            cu[0] += ws * R(2) * (u[0] - A.obj.uref[0]);
+            cu[1] += ws * R(2) * (u[1] - A.obj.uref[1]);
+            if (L::D == 3) cu[2] += ws * R(2) * (u[2] - A.obj.uref[2]);
+            break;
+          }
+          case OBJ_PRES: crho += ws * c; break;
+          default: {
+            cm[0] += ws * R(-2) * gi;
+            gt += ws * R(-2) * M.m[0];   // direct d psi / d g, times g'(phi) later
+          }
+        }
+      }
+    }
+  }
+  // tau_eff(|Pi|, rho) of Eq. 14: d te/d|Pi| = 4.5 C^2/(s rho), d te/d rho = -4.5 C^2 |Pi|/(s rho^2) (Eq. 32)
+  {
+    const R k1 = R(4.5) * A.ph.c2 / (M.s * M.rho);      // d te / d|Pi|
+    crho += ctau * (-k1 * M.pn * M.inv);
+    if (M.pn > R(0)) {
+      const R kp = ctau * k1 * R(2) / M.pn;            // times d|Pi|/dPi = 2 Pi / |Pi|
+#pragma unroll
+      for (int k = 0; k < 6; ++k) cpi[k] += kp * M.pi[k];
+    }
+  }
+  // u = m / rho
+  R gm[3], grho;
+  gm[0] = cu[0] * M.inv + cm[0];
+  gm[1] = cu[1] * M.inv + cm[1];
+  gm[2] = cu[2] * M.inv + cm[2];
+  grho = crho - (u[0] * cu[0] + u[1] * cu[1] + u[2] * cu[2]) * M.inv;
+  // Pi(rho, m, M2) = M2 - rho cs^2 I - m m^T / rho
+  {
+    const R* m = M.m;
+    const R pm0 = cpi[0] * m[0] + cpi[3] * m[1] + cpi[4] * m[2];
+    const R pm1 = cpi[3] * m[0] + cpi[1] * m[1] + cpi[5] * m[2];
+    const R pm2 = cpi[4] * m[0] + cpi[5] * m[1] + cpi[2] * m[2];
+    grho += -c * (cpi[0] + cpi[1] + cpi[2]) + (m[0] * pm0 + m[1] * pm1 + m[2] * pm2) * M.inv * M.inv;
+    gm[0] -= R(2) * pm0 * M.inv;
+    gm[1] -= R(2) * pm1 * M.inv;
+    gm[2] -= R(2) * pm2 * M.inv;
+  }
+  // b_a = d psi / d f_a = grho + c_a . gm + c_a c_a : cpi
+  R b[L::Q];
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) {
+    const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
+    b[k] = grho + R(cx) * gm[0] + R(cy) * gm[1] + R(cz) * gm[2] + R(cx * cx) * cpi[0] +
+           R(cy * cy) * cpi[1] + R(cz * cz) * cpi[2] + R(2 * cx * cy) * cpi[3] + R(2 * cx * cz) * cpi[4] +
+           R(2 * cy * cz) * cpi[5];
+  }
+  if (face) bc_transpose<L, R>(b, unk, cls, u0, A.ph.rho_out);
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) A.bout[k * g.n + i] = b[k];
+
+  const int* d = A.dbox;
+  if (x >= d[0] && x < d[1] && y >= d[2] && y < d[3] && z >= d[4] && z < d[5]) {
+    double2 s = A.gacc[i];
+    neumaier(s.x, s.y, double(gt));
+    A.gacc[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels: design field, gradient, state conversion, checkpoints.
+// ---------------------------------------------------------------------------
+
+// g(phi) = g_max (1 - phi (1+q)/(phi+q)), phi = 1 - gamma  (Sec. 2.2)
+template <class R>
+__global__ void design_kernel(const float* __restrict__ gamma, R* __restrict__ gf, long long n, double q,
+                              double g_max, int* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gm = gamma[i];
+    if (!(gm >= 0.f && gm <= 1.f)) *bad = 1;
+    const double phi = 1.0 - double(gm);
+    gf[i] = R(g_max * (1.0 - phi * (1.0 + q) / (phi + q)));
+  }
+}
+
+// dJ/dgamma = -g'(phi) * G = g_max q (1+q) / (phi+q)^2 * G inside the design box.
+__global__ void gradient_kernel(const double2* __restrict__ gacc, const float* __restrict__ gamma,
+                                double* __restrict__ out, Geo g, int x0, int x1, int y0, int y1,
+                                int z0, int z1, double q, double g_max) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = int(i % g.nx), y = int((i / g.nx) % g.ny), z = int(i / g.sz);
+    double v = 0.0;
+    if (x >= x0 && x < x1 && y >= y0 && y < y1 && z >= z0 && z < z1) {
+      const double phi = 1.0 - double(gamma[i]);
+      const double dgp = g_max * q * (1.0 + q) / ((phi + q) * (phi + q));
+      const double2 s = gacc[i];
+      v = dgp * (s.x + s.y);
+    }
+    out[i] = v;
+  }
+}
+
+template <class L, class R>
+__global__ void unshift_kernel(const R* __restrict__ src, double* __restrict__ dst, long long n) {
+  const long long total = n * L::Q;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int a = int(k / n);
+    double w = 0;
+#pragma unroll
+    for (int b = 0; b < L::Q; ++b) if (b == a) w = L::w(b);
+    dst[k] = double(src[k]) + w;
+  }
+}
+
+template <class L, class R>
+__global__ void shift_kernel(const double* __restrict__ src, R* __restrict__ dst, long long n, int* bad) {
+  const long long total = n * L::Q;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int a = int(k / n);
+    double w = 0;
+#pragma unroll
+    for (int b = 0; b < L::Q; ++b) if (b == a) w = L::w(b);
+    const double v = src[k];
+    if (!isfinite(v)) *bad = 1;
+    dst[k] = R(v - w);
+  }
+}
+
+template <class R>
+__global__ void copy_double_kernel(const R* __restrict__ src, double* __restrict__ dst, long long total) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x)
+    dst[k] = double(src[k]);
+}
+
+// 16-bit checkpoints: deviation from the equilibrium of the stored field's own
+// moments, scaled per block of kBlock nodes by a power of two so that the
+// block's largest deviation sits near 2^14, plus rho-1 and m in FP32.
+template <class T> __device__ __forceinline__ T to16(float v);
+template <> __device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from16(__half v) { return __half2float(v); }
+__device__ __forceinline__ float from16(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class L>
+__device__ __forceinline__ float feq_shifted(float rt, float rho, const float (&u)[3], int a) {
+  const float cu = L::cx(a) * u[0] + L::cy(a) * u[1] + L::cz(a) * u[2];
+  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  return float(L::w(a)) * (rt + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
+}
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock) ckpt_encode_kernel(const float* __restrict__ p, T* __restrict__ dev,
+                                                             float* __restrict__ mom, int* __restrict__ expo,
+                                                             long long n) {
+  __shared__ float smax[kBlock / 32];
+  const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+  float f[L::Q], d[L::Q];
+  float mx = 0.f;
+  float rt = 0.f, u[3] = {0.f, 0.f, 0.f}, rho = 1.f;
+  if (i < n) {
+    float m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+      f[a] = p[a * n + i];
+      rt += f[a];
+      m[0] += L::cx(a) * f[a];
+      m[1] += L::cy(a) * f[a];
+      m[2] += L::cz(a) * f[a];
+    }
+    rho = 1.f + rt;
+    u[0] = m[0] / rho; u[1] = m[1] / rho; u[2] = m[2] / rho;
+    mom[i] = rt;
+    mom[n + i] = m[0];
+    mom[2 * n + i] = m[1];
+    if (L::D == 3) mom[3 * n + i] = m[2];
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+      d[a] = f[a] - feq_shifted<L>(rt, rho, u, a);
+      mx = fmaxf(mx, fabsf(d[a]));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float bmax = 0.f;
+#pragma unroll
+  for (int k = 0; k < kBlock / 32; ++k) bmax = fmaxf(bmax, smax[k]);
+  int e = 0;
+  if (bmax > 0.f) { frexpf(bmax, &e); e = 14 - e; }   // scale = 2^e puts bmax in [2^13, 2^14)
+  if (threadIdx.x == 0) expo[blockIdx.x] = e;
+  if (i < n) {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) dev[a * n + i] = to16<T>(ldexpf(d[a], e));
+  }
+}
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock) ckpt_decode_kernel(const T* __restrict__ dev, const float* __restrict__ mom,
+                                                             const int* __restrict__ expo, float* __restrict__ p,
+                                                             long long n) {
+  const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+  if (i >= n) return;
+  const int e = expo[blockIdx.x];
+  const float rt = mom[i];
+  const float rho = 1.f + rt;
+  float u[3] = {mom[n + i] / rho, mom[2 * n + i] / rho, L::D == 3 ? mom[3 * n + i] / rho : 0.f};
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) p[a * n + i] = feq_shifted<L>(rt, rho, u, a) + ldexpf(from16(dev[a * n + i]), -e);
+}
+
+}  // namespace lbm

@@ -1,0 +1,728 @@
+// Host side of the C ABI declared in include/lbmadj.h: configuration checks,
+// workspace carving, the window / adjoint drivers and their launches.
+//
+// The forward window runs |W| fused collide-stream launches, copying (or
+// 16-bit encoding) the carried field into checkpoint slot s before step
+// n0 + s K.  The adjoint walks the segments backward: it restores segment s
+// from its checkpoint, recomputes its K-1 later states into the segment
+// buffer with the same forward kernel (bitwise the same trajectory for
+// native checkpoints), then runs K adjoint launches from the last state to
+// the first.  The design sensitivity of every adjoint step is added into a
+// per-node FP64 (sum, compensation) pair.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "lbmadj.h"
+#include "kernels.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lbm_status fail(lbm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define LBM_TRY(expr)              \
+  do {                             \
+    lbm_status s_ = (expr);        \
+    if (s_ != LBM_OK) return s_;   \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+template <class L>
+unsigned unknown_mask(const lbm_config& c, int x, int y, int z) {
+  unsigned m = 0;
+  for (int a = 0; a < L::Q; ++a) {
+    const int X = x - L::cx(a), Y = y - L::cy(a), Z = z - L::cz(a);
+    bool out = false;
+    if (!c.periodic[0] && (X < 0 || X >= c.nx)) out = true;
+    if (!c.periodic[1] && (Y < 0 || Y >= c.ny)) out = true;
+    if (!c.periodic[2] && (Z < 0 || Z >= c.nz)) out = true;
+    if (out) m |= 1u << a;
+  }
+  return m;
+}
+
+template <class L>
+unsigned mask_with_cx(int sx) {
+  unsigned m = 0;
+  for (int a = 0; a < L::Q; ++a)
+    if (L::cx(a) == sx) m |= 1u << a;
+  return m;
+}
+
+// Layout of the caller's workspace.
+struct Layout {
+  size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
+      partials, counter, acc, flags, total;
+  int nblocks_fwd, nblocks_1d, nslots;
+  bool stage_in_seg;
+};
+
+lbm_status validate_config(const lbm_config& c) {
+  if (c.lattice != LBM_D2Q9 && c.lattice != LBM_D3Q19) return fail(LBM_ERR_ARG, "lattice must be 9 or 19");
+  if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(LBM_ERR_ARG, "lattice sizes must be >= 1");
+  if (c.lattice == LBM_D2Q9 && c.nz != 1) return fail(LBM_ERR_ARG, "D2Q9 needs nz == 1");
+  if (c.ny > 65535 || c.nz > 65535) return fail(LBM_ERR_ARG, "ny and nz must be <= 65535");
+  const int dims[3] = {c.nx, c.ny, c.nz};
+  for (int k = 0; k < 3; ++k) {
+    if (c.periodic[k] != 0 && c.periodic[k] != 1) return fail(LBM_ERR_ARG, "periodic flags must be 0 or 1");
+    const bool used = k < 2 || c.lattice == LBM_D3Q19;
+    if (used && !c.periodic[k] && dims[k] < 3) return fail(LBM_ERR_ARG, "a bounded axis needs >= 3 nodes");
+  }
+  if (c.precision != LBM_FP32 && c.precision != LBM_FP64) return fail(LBM_ERR_ARG, "precision must be FP32 or FP64");
+  if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(LBM_ERR_ARG, "tau must be > 0.5");
+  if (!(c.cs_smag >= 0.0) || !std::isfinite(c.cs_smag)) return fail(LBM_ERR_ARG, "cs_smag must be >= 0");
+  if (!(c.q_interp > 0.0) || !std::isfinite(c.q_interp)) return fail(LBM_ERR_ARG, "q_interp must be > 0");
+  if (!(c.g_max >= 0.0 && c.g_max <= 1.0)) return fail(LBM_ERR_ARG, "g_max must be in [0, 1]");
+  if (!(c.rho_out > 0.0) || !std::isfinite(c.rho_out)) return fail(LBM_ERR_ARG, "rho_out must be > 0");
+  if (c.objective_kind < 0 || c.objective_kind > 3) return fail(LBM_ERR_ARG, "objective_kind out of range");
+  if (c.monitor_kind < 0 || c.monitor_kind > 1) return fail(LBM_ERR_ARG, "monitor_kind out of range");
+  if (c.monitor_kind == LBM_MON_DRAG && !(c.monitor_u > 0.0 && c.monitor_l > 0.0))
+    return fail(LBM_ERR_ARG, "monitor_u and monitor_l must be > 0 for the drag monitor");
+  if (c.window_len < 1) return fail(LBM_ERR_ARG, "window_len must be >= 1");
+  if (c.sample_every < 1 || c.window_len % c.sample_every) return fail(LBM_ERR_ARG, "sample_every must divide window_len");
+  if (c.ckpt_every < 1 || c.window_len % c.ckpt_every) return fail(LBM_ERR_ARG, "ckpt_every must divide window_len");
+  if (c.ckpt_format < 0 || c.ckpt_format > 2) return fail(LBM_ERR_ARG, "ckpt_format out of range");
+  if (c.ckpt_format != LBM_CKPT_NATIVE && c.precision != LBM_FP32)
+    return fail(LBM_ERR_ARG, "16-bit checkpoints need the FP32 solver");
+  if (!(c.conv_tol >= 0.0)) return fail(LBM_ERR_ARG, "conv_tol must be >= 0");
+  for (const int32_t* bx : {c.obj_box, c.design_box})
+    for (int k = 0; k < 3; ++k)
+      if (bx[2 * k] < 0 || bx[2 * k] > bx[2 * k + 1] || bx[2 * k + 1] > dims[k])
+        return fail(LBM_ERR_ARG, "box bounds must satisfy 0 <= lo <= hi <= size");
+  return LBM_OK;
+}
+
+Layout make_layout(const lbm_config& c) {
+  Layout L{};
+  const size_t n = size_t(c.nx) * c.ny * c.nz;
+  const int q = c.lattice;
+  const int d = c.lattice == LBM_D2Q9 ? 2 : 3;
+  const size_t rs = c.precision == LBM_FP64 ? 8 : 4;
+  const size_t lat = align_up(size_t(q) * n * rs);
+  L.nblocks_fwd = ((c.nx + lbm::kBlock - 1) / lbm::kBlock) * c.ny * c.nz;
+  L.nblocks_1d = int((n + lbm::kBlock - 1) / lbm::kBlock);
+  L.nslots = c.window_len / c.ckpt_every;
+  const bool native = c.ckpt_format == LBM_CKPT_NATIVE;
+  L.ckpt_slot = native ? lat
+                       : align_up(size_t(q) * n * 2) + align_up(size_t(d + 1) * n * 4) +
+                             align_up(size_t(L.nblocks_1d) * 4);
+  L.seg_slots = native ? size_t(c.ckpt_every - 1) : size_t(c.ckpt_every);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+  L.f[0] = take(lat);
+  L.f[1] = take(lat);
+  L.b[0] = take(lat);
+  L.b[1] = take(lat);
+  L.g = take(n * rs);
+  L.gamma = take(n * 4);
+  L.wobj = take(n * 4);
+  L.cls = take(n);
+  L.uin = take(size_t(c.ny) * c.nz * 4);
+  L.gacc = take(n * 16);
+  L.gout = take(n * 8);
+  L.partials = take(size_t(L.nblocks_fwd) * 16);
+  L.counter = take(16);
+  L.acc = take(sizeof(lbm::WindowAcc));
+  L.flags = take(16);
+  L.ckpt = take(L.ckpt_slot * L.nslots);
+  L.seg = take(lat * L.seg_slots);
+  const size_t stage_bytes = size_t(q) * n * 8;
+  L.stage_in_seg = lat * L.seg_slots >= stage_bytes;
+  L.stage = L.stage_in_seg ? L.seg : take(stage_bytes);
+  L.total = off;
+  return L;
+}
+
+struct Pending {
+  int phase;
+  cudaEvent_t a, b;
+  int64_t launches, lus;
+};
+
+}  // namespace
+
+// Polymorphic per-(lattice, precision) implementation.
+struct Impl {
+  virtual ~Impl() = default;
+  virtual void fwd(const void* src, void* dst, int sample) = 0;
+  virtual void adj(const void* bnext, const void* pprev, void* bout, int sample) = 0;
+  virtual void pull(const void* b, void* out) = 0;
+  virtual void set_design() = 0;
+  virtual void grad() = 0;
+  virtual void unshift(const void* src) = 0;
+  virtual void shift(void* dst) = 0;
+  virtual void to_double(const void* src) = 0;
+  virtual void encode(const void* p, int slot) = 0;
+  virtual void decode(int slot, void* p) = 0;
+};
+
+struct lbm_ctx {
+  lbm_config cfg;
+  Layout lay;
+  char* ws;
+  cudaStream_t stream;
+  lbm::Geo geo;
+  size_t n, q, rs;
+  int cur;                    // index of the buffer holding the carried field
+  int64_t steps = 0, windows = 0;
+  bool window_valid = false, grad_valid = false;
+  double last_j = 0, last_m = 0, ratio = INFINITY;
+  int converged = 0, nwin_for_ratio = 0;
+  int bout_last = 0;          // adjoint buffer holding b^{n0}
+  double jconst = 0;
+  bool timing = false;
+  lbm_timing tm{};
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  std::unique_ptr<Impl> impl;
+
+  template <class T = void>
+  T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+  void* lattice(int k) const { return ws + lay.f[k]; }
+  void* adjbuf(int k) const { return ws + lay.b[k]; }
+  void* seg_slot(int s, int j) const {   // state p^{n0 + sK - 1 + j}
+    const size_t lat = align_up(q * n * rs);
+    if (cfg.ckpt_format == LBM_CKPT_NATIVE) {
+      if (j == 0) return ws + lay.ckpt + lay.ckpt_slot * s;
+      return ws + lay.seg + lat * (j - 1);
+    }
+    return ws + lay.seg + lat * j;
+  }
+
+  cudaEvent_t event() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  // Phase bracket: call begin() before and end() after a run of launches.
+  cudaEvent_t begin() {
+    if (!timing) return nullptr;
+    cudaEvent_t e = event();
+    if (e) cudaEventRecord(e, stream);
+    return e;
+  }
+  void end(cudaEvent_t a, int phase, int64_t launches, int64_t lus) {
+    if (!timing || !a) return;
+    cudaEvent_t b = event();
+    if (!b) return;
+    cudaEventRecord(b, stream);
+    pending.push_back({phase, a, b, launches, lus});
+  }
+  void harvest() {   // after a stream synchronisation
+    for (auto& p : pending) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        tm.ms[p.phase] += ms;
+        tm.launches[p.phase] += p.launches;
+        tm.lattice_updates[p.phase] += p.lus;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  ~lbm_ctx() {
+    for (auto& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+template <class L, class R>
+struct ImplT final : Impl {
+  lbm_ctx* c;
+  explicit ImplT(lbm_ctx* ctx) : c(ctx) {}
+
+  dim3 grid() const { return dim3((c->cfg.nx + lbm::kBlock - 1) / lbm::kBlock, c->cfg.ny, c->cfg.nz); }
+  int flat_blocks() const {
+    long long b = (long long)(c->n * c->q + 255) / 256;
+    return int(b < 148 * 32 ? b : 148 * 32);
+  }
+  lbm::Phys<R> phys() const { return {R(c->cfg.tau), R(c->cfg.cs_smag * c->cfg.cs_smag), R(c->cfg.rho_out)}; }
+  lbm::Obj<R> obj() const {
+    lbm::Obj<R> o{};
+    const lbm_config& k = c->cfg;
+    o.kind = k.objective_kind;
+    o.mon = k.monitor_kind;
+    for (int i = 0; i < 3; ++i) o.uref[i] = R(k.objective_uref[i]);
+    for (int i = 0; i < 6; ++i) o.box[i] = k.obj_box[i];
+    o.ws = R(double(k.sample_every) / double(k.window_len));
+    o.mon_scale = k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
+    o.jconst = c->jconst;
+    return o;
+  }
+
+  void fwd(const void* src, void* dst, int sample) override {
+    lbm::FwdArgs<R> A;
+    A.src = static_cast<const R*>(src);
+    A.dst = static_cast<R*>(dst);
+    A.gfield = c->template at<R>(c->lay.g);
+    A.cls = c->template at<uint8_t>(c->lay.cls);
+    A.uin = c->template at<float>(c->lay.uin);
+    A.wobj = c->template at<float>(c->lay.wobj);
+    A.geo = c->geo;
+    A.ph = phys();
+    A.obj = obj();
+    A.sample = sample;
+    A.partials = c->template at<double>(c->lay.partials);
+    A.counter = c->template at<unsigned>(c->lay.counter);
+    A.acc = c->template at<lbm::WindowAcc>(c->lay.acc);
+    A.nonfinite = c->template at<int>(c->lay.flags);
+    lbm::fwd_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->stream>>>(A);
+  }
+  void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
+    lbm::AdjArgs<R> A;
+    A.bnext = static_cast<const R*>(bnext);
+    A.pprev = static_cast<const R*>(pprev);
+    A.bout = static_cast<R*>(bout);
+    A.gfield = c->template at<R>(c->lay.g);
+    A.cls = c->template at<uint8_t>(c->lay.cls);
+    A.uin = c->template at<float>(c->lay.uin);
+    A.wobj = c->template at<float>(c->lay.wobj);
+    A.gacc = c->template at<double2>(c->lay.gacc);
+    A.geo = c->geo;
+    A.ph = phys();
+    A.obj = obj();
+    A.sample = sample;
+    A.terminal = bnext == nullptr;
+    for (int i = 0; i < 6; ++i) A.dbox[i] = c->cfg.design_box[i];
+    lbm::adj_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->stream>>>(A);
+  }
+  void pull(const void* b, void* out) override {
+    lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->stream>>>(
+        static_cast<const R*>(b), c->template at<uint8_t>(c->lay.cls), static_cast<R*>(out), c->geo);
+  }
+  void set_design() override {
+    lbm::design_kernel<R><<<flat_blocks(), 256, 0, c->stream>>>(
+        c->template at<float>(c->lay.gamma), c->template at<R>(c->lay.g), (long long)c->n, c->cfg.q_interp, c->cfg.g_max, c->template at<int>(c->lay.flags) + 1);
+  }
+  void grad() override {
+    const int* d = c->cfg.design_box;
+    lbm::gradient_kernel<<<flat_blocks(), 256, 0, c->stream>>>(
+        c->template at<double2>(c->lay.gacc), c->template at<float>(c->lay.gamma), c->template at<double>(c->lay.gout),
+        c->geo, d[0], d[1], d[2], d[3], d[4], d[5], c->cfg.q_interp, c->cfg.g_max);
+  }
+  void unshift(const void* src) override {
+    lbm::unshift_kernel<L, R><<<flat_blocks(), 256, 0, c->stream>>>(static_cast<const R*>(src),
+                                                                      c->template at<double>(c->lay.stage),
+                                                                      (long long)c->n);
+  }
+  void shift(void* dst) override {
+    lbm::shift_kernel<L, R><<<flat_blocks(), 256, 0, c->stream>>>(c->template at<double>(c->lay.stage),
+                                                                    static_cast<R*>(dst), (long long)c->n,
+                                                                    c->template at<int>(c->lay.flags) + 1);
+  }
+  void to_double(const void* src) override {
+    lbm::copy_double_kernel<R><<<flat_blocks(), 256, 0, c->stream>>>(
+        static_cast<const R*>(src), c->template at<double>(c->lay.stage), (long long)(c->n * c->q));
+  }
+  template <class T>
+  void encode_t(const void* p, int slot) {
+    char* base = c->ws + c->lay.ckpt + c->lay.ckpt_slot * slot;
+    T* dev = reinterpret_cast<T*>(base);
+    float* mom = reinterpret_cast<float*>(base + align_up(c->q * c->n * 2));
+    int* ex = reinterpret_cast<int*>(base + align_up(c->q * c->n * 2) + align_up((L::D + 1) * c->n * 4));
+    lbm::ckpt_encode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->stream>>>(
+        static_cast<const float*>(p), dev, mom, ex, (long long)c->n);
+  }
+  template <class T>
+  void decode_t(int slot, void* p) {
+    char* base = c->ws + c->lay.ckpt + c->lay.ckpt_slot * slot;
+    T* dev = reinterpret_cast<T*>(base);
+    float* mom = reinterpret_cast<float*>(base + align_up(c->q * c->n * 2));
+    int* ex = reinterpret_cast<int*>(base + align_up(c->q * c->n * 2) + align_up((L::D + 1) * c->n * 4));
+    lbm::ckpt_decode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->stream>>>(
+        dev, mom, ex, static_cast<float*>(p), (long long)c->n);
+  }
+  void encode(const void* p, int slot) override {
+    if constexpr (sizeof(R) == 4) {
+      if (c->cfg.ckpt_format == LBM_CKPT_FP16) encode_t<__half>(p, slot); else encode_t<__nv_bfloat16>(p, slot);
+    }
+  }
+  void decode(int slot, void* p) override {
+    if constexpr (sizeof(R) == 4) {
+      if (c->cfg.ckpt_format == LBM_CKPT_FP16) decode_t<__half>(slot, p); else decode_t<__nv_bfloat16>(slot, p);
+    }
+  }
+};
+
+template <class L>
+lbm_status validate_classes(const lbm_config& c, const uint8_t* cls) {
+  const unsigned in_mask = mask_with_cx<L>(1);
+  for (int z = 0; z < c.nz; ++z)
+    for (int y = 0; y < c.ny; ++y)
+      for (int x = 0; x < c.nx; ++x) {
+        const size_t i = size_t(x) + size_t(c.nx) * (size_t(y) + size_t(c.ny) * z);
+        const uint8_t k = cls[i];
+        if (k > LBM_OUTLET_ZEROGRAD) return fail(LBM_ERR_ARG, "node %zu: class %d out of range", i, int(k));
+        const bool face = x == 0 || x == c.nx - 1 || y == 0 || y == c.ny - 1 ||
+                          (L::D == 3 && (z == 0 || z == c.nz - 1));
+        if (!face) {
+          if (k != LBM_FLUID) return fail(LBM_ERR_ARG, "node %zu: interior nodes must be FLUID", i);
+          continue;
+        }
+        const unsigned unk = unknown_mask<L>(c, x, y, z);
+        switch (k) {
+          case LBM_FLUID:
+            if (unk) return fail(LBM_ERR_ARG, "node %zu: boundary node with unknown populations is FLUID", i);
+            break;
+          case LBM_WALL: break;
+          case LBM_INLET: {
+            const unsigned want = L::Q == 9 ? ((1u << 1) | (1u << 5) | (1u << 8)) : in_mask;
+            if (x != 0 || unk != want)
+              return fail(LBM_ERR_ARG, "node %zu: inlet nodes must lie on the x=0 face away from other faces", i);
+            break;
+          }
+          case LBM_OUTLET_PRESSURE:
+            if (L::Q != 9 || x != c.nx - 1 || unk != ((1u << 3) | (1u << 6) | (1u << 7)))
+              return fail(LBM_ERR_ARG, "node %zu: pressure outlets are D2Q9 nodes on the x=nx-1 face away from walls", i);
+            break;
+          case LBM_OUTLET_ZEROGRAD: {
+            if (c.periodic[0] || !(x == 0 || x == c.nx - 1))
+              return fail(LBM_ERR_ARG, "node %zu: zero-gradient outlets lie on a bounded x face", i);
+            const unsigned want = mask_with_cx<L>(x == 0 ? 1 : -1);
+            if (unk != want)
+              return fail(LBM_ERR_ARG, "node %zu: zero-gradient outlet must not touch another face", i);
+            break;
+          }
+        }
+      }
+  return LBM_OK;
+}
+
+lbm_status check_flags(lbm_ctx* c, int which, lbm_status st, const char* what) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, c->at<int>(c->lay.flags) + which, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (h) {
+    CUDA_TRY(cudaMemsetAsync(c->at<int>(c->lay.flags) + which, 0, sizeof(int), c->stream));
+    return fail(st, "%s", what);
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_STATE: return "call out of order";
+    case LBM_ERR_NONFINITE: return "non-finite or non-positive density";
+    case LBM_NOT_CONVERGED: return "not converged";
+  }
+  return "unknown status";
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+lbm_status lbm_workspace_size(const lbm_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes) return fail(LBM_ERR_ARG, "null argument");
+  LBM_TRY(validate_config(*cfg));
+  *bytes = make_layout(*cfg).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const float* design_gamma,
+                      const float* objective_weights, const float* inlet_u, void* workspace,
+                      size_t workspace_bytes, void* stream, lbm_ctx** out) {
+  if (!cfg || !node_class || !design_gamma || !out) return fail(LBM_ERR_ARG, "null argument");
+  *out = nullptr;
+  LBM_TRY(validate_config(*cfg));
+  const lbm_config& c = *cfg;
+  LBM_TRY(c.lattice == LBM_D2Q9 ? validate_classes<D2Q9>(c, node_class) : validate_classes<D3Q19>(c, node_class));
+  const Layout lay = make_layout(c);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign))
+    return fail(LBM_ERR_WORKSPACE, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < lay.total)
+    return fail(LBM_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, lay.total);
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, workspace) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(LBM_ERR_WORKSPACE, "workspace is not device memory");
+  }
+
+  auto ctx = std::make_unique<lbm_ctx>();
+  ctx->cfg = c;
+  ctx->lay = lay;
+  ctx->ws = static_cast<char*>(workspace);
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->n = size_t(c.nx) * c.ny * c.nz;
+  ctx->q = c.lattice;
+  ctx->rs = c.precision == LBM_FP64 ? 8 : 4;
+  ctx->geo = lbm::Geo{c.nx, c.ny, c.nz, c.periodic[0], c.periodic[1], c.periodic[2], (long long)ctx->n,
+                      (long long)c.nx, (long long)c.nx * c.ny};
+  ctx->cur = 0;
+  lbm_ctx* x = ctx.get();
+  if (c.lattice == LBM_D2Q9) {
+    if (c.precision == LBM_FP32) ctx->impl.reset(new ImplT<D2Q9, float>(x));
+    else ctx->impl.reset(new ImplT<D2Q9, double>(x));
+  } else {
+    if (c.precision == LBM_FP32) ctx->impl.reset(new ImplT<D3Q19, float>(x));
+    else ctx->impl.reset(new ImplT<D3Q19, double>(x));
+  }
+  const size_t n = ctx->n;
+  cudaStream_t s = ctx->stream;
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.f[0]), 0, align_up(ctx->q * n * ctx->rs), s));   // rest equilibrium
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.counter), 0, 16, s));
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.acc), 0, sizeof(lbm::WindowAcc), s));
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.flags), 0, 16, s));
+  CUDA_TRY(cudaMemcpyAsync(x->at(lay.cls), node_class, n, cudaMemcpyDefault, s));
+  CUDA_TRY(cudaMemcpyAsync(x->at(lay.gamma), design_gamma, n * 4, cudaMemcpyDefault, s));
+  if (objective_weights) CUDA_TRY(cudaMemcpyAsync(x->at(lay.wobj), objective_weights, n * 4, cudaMemcpyDefault, s));
+  else CUDA_TRY(cudaMemsetAsync(x->at(lay.wobj), 0, n * 4, s));
+  if (inlet_u) CUDA_TRY(cudaMemcpyAsync(x->at(lay.uin), inlet_u, size_t(c.ny) * c.nz * 4, cudaMemcpyDefault, s));
+  else CUDA_TRY(cudaMemsetAsync(x->at(lay.uin), 0, size_t(c.ny) * c.nz * 4, s));
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.gacc), 0, n * 16, s));
+  // Constant part of a pressure objective: cs^2 * sum of weights (FP64, host).
+  if (c.objective_kind == LBM_OBJ_PRESSURE) {
+    std::vector<float> w(n, 0.f);
+    if (objective_weights) {
+      CUDA_TRY(cudaMemcpyAsync(w.data(), objective_weights, n * 4, cudaMemcpyDefault, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    double sw = 0, cw = 0;
+    const int* b = c.obj_box;
+    for (int z = b[4]; z < b[5]; ++z)
+      for (int y = b[2]; y < b[3]; ++y)
+        for (int xx = b[0]; xx < b[1]; ++xx) {
+          const double v = w[size_t(xx) + size_t(c.nx) * (size_t(y) + size_t(c.ny) * z)];
+          const double t = sw + v;
+          cw += std::fabs(sw) >= std::fabs(v) ? (sw - t) + v : (v - t) + sw;
+          sw = t;
+        }
+    ctx->jconst = (sw + cw) / 3.0;
+  }
+  {
+    std::vector<float> u(size_t(c.ny) * c.nz, 0.f);
+    if (inlet_u) {
+      CUDA_TRY(cudaMemcpyAsync(u.data(), inlet_u, u.size() * 4, cudaMemcpyDefault, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    for (float v : u)
+      if (!(std::fabs(v) < 0.5f)) return fail(LBM_ERR_ARG, "inlet velocities must satisfy |u| < 0.5");
+  }
+  x->impl->set_design();
+  CUDA_TRY(cudaGetLastError());
+  LBM_TRY(check_flags(x, 1, LBM_ERR_ARG, "design values must lie in [0, 1]"));
+  *out = ctx.release();
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* ctx) { delete ctx; }
+
+lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  const lbm_config& k = c->cfg;
+  const int K = k.ckpt_every, S = c->lay.nslots;
+  const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
+  const size_t lat_bytes = c->q * c->n * c->rs;
+  for (int s = 0; s < S; ++s) {
+    cudaEvent_t e = c->begin();
+    if (native) CUDA_TRY(cudaMemcpyAsync(c->seg_slot(s, 0), c->lattice(c->cur), lat_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    else c->impl->encode(c->lattice(c->cur), s);
+    c->end(e, 3, 1, 0);
+    e = c->begin();
+    for (int j = 0; j < K; ++j) {
+      const int step = s * K + j;
+      c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0);
+      c->cur ^= 1;
+    }
+    c->end(e, 0, K, int64_t(K) * int64_t(c->n));
+  }
+  lbm::window_end_kernel<<<1, 32, 0, c->stream>>>(c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol, c->at<int>(c->lay.flags));
+  CUDA_TRY(cudaGetLastError());
+  lbm::WindowAcc acc;
+  CUDA_TRY(cudaMemcpyAsync(&acc, c->at(c->lay.acc), sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->harvest();
+  c->steps += k.window_len;
+  if (acc.nonfinite) {
+    c->window_valid = false;
+    c->grad_valid = false;
+    return fail(LBM_ERR_NONFINITE, "window %lld produced a non-positive density or a non-finite value",
+                (long long)c->windows);
+  }
+  c->windows += 1;
+  c->window_valid = true;
+  c->grad_valid = false;
+  c->last_j = acc.jmean;
+  c->last_m = acc.mmean;
+  c->nwin_for_ratio += 1;
+  c->ratio = c->nwin_for_ratio >= 2 ? acc.ratio : INFINITY;
+  c->converged = c->nwin_for_ratio >= 2 ? acc.converged : 0;
+  if (J_window) *J_window = acc.jmean;
+  if (monitor_window) *monitor_window = acc.mmean;
+  return LBM_OK;
+}
+
+lbm_status lbm_window_converged(lbm_ctx* c, int* converged, double* ratio) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (converged) *converged = c->converged;
+  if (ratio) *ratio = c->ratio;
+  return LBM_OK;
+}
+
+lbm_status lbm_adjoint_window(lbm_ctx* c, double* J_eff) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (!c->window_valid) return fail(LBM_ERR_STATE, "no completed window to differentiate");
+  const lbm_config& k = c->cfg;
+  const int K = k.ckpt_every, S = c->lay.nslots;
+  const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
+  CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gacc), 0, c->n * 16, c->stream));
+  int bo = 0;
+  const void* bnext = nullptr;
+  for (int s = S - 1; s >= 0; --s) {
+    cudaEvent_t e = c->begin();
+    if (!native) c->impl->decode(s, c->seg_slot(s, 0));
+    c->end(e, 3, native ? 0 : 1, 0);
+    e = c->begin();
+    for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
+    c->end(e, 1, K - 1, int64_t(K - 1) * int64_t(c->n));
+    e = c->begin();
+    for (int j = K - 1; j >= 0; --j) {
+      const int step = s * K + j;
+      c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), step % k.sample_every == 0);
+      bnext = c->adjbuf(bo);
+      bo ^= 1;
+    }
+    c->end(e, 2, K, int64_t(K) * int64_t(c->n));
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->harvest();
+  c->bout_last = bo ^ 1;
+  c->grad_valid = true;
+  if (J_eff) *J_eff = c->last_j;
+  return LBM_OK;
+}
+
+lbm_status lbm_design_gradient(lbm_ctx* c, double* grad, size_t n) {
+  if (!c || !grad) return fail(LBM_ERR_ARG, "null argument");
+  if (!c->grad_valid) return fail(LBM_ERR_STATE, "no adjoint window computed");
+  if (n != c->n) return fail(LBM_ERR_ARG, "gradient length %zu, expected %zu", n, c->n);
+  c->impl->grad();
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(grad, c->at(c->lay.gout), n * 8, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_design(lbm_ctx* c, const float* gamma) {
+  if (!c || !gamma) return fail(LBM_ERR_ARG, "null argument");
+  CUDA_TRY(cudaMemcpyAsync(c->at(c->lay.gamma), gamma, c->n * 4, cudaMemcpyDefault, c->stream));
+  c->impl->set_design();
+  CUDA_TRY(cudaGetLastError());
+  c->window_valid = false;
+  c->grad_valid = false;
+  c->nwin_for_ratio = 0;
+  return check_flags(c, 1, LBM_ERR_ARG, "design values must lie in [0, 1]");
+}
+
+lbm_status lbm_get_state(lbm_ctx* c, double* f, size_t n) {
+  if (!c || !f) return fail(LBM_ERR_ARG, "null argument");
+  if (n != c->n * c->q) return fail(LBM_ERR_ARG, "state length %zu, expected %zu", n, c->n * c->q);
+  c->impl->unshift(c->lattice(c->cur));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(f, c->at(c->lay.stage), n * 8, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const double* f, size_t n) {
+  if (!c || !f) return fail(LBM_ERR_ARG, "null argument");
+  if (n != c->n * c->q) return fail(LBM_ERR_ARG, "state length %zu, expected %zu", n, c->n * c->q);
+  CUDA_TRY(cudaMemcpyAsync(c->at(c->lay.stage), f, n * 8, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->at<int>(c->lay.flags), 0, sizeof(int), c->stream));   // clear the sticky non-finite flag
+  c->impl->shift(c->lattice(c->cur));
+  CUDA_TRY(cudaGetLastError());
+  c->window_valid = false;
+  c->grad_valid = false;
+  c->nwin_for_ratio = 0;
+  return check_flags(c, 1, LBM_ERR_ARG, "state holds non-finite values");
+}
+
+lbm_status lbm_get_adjoint_state(lbm_ctx* c, double* a, size_t n) {
+  if (!c || !a) return fail(LBM_ERR_ARG, "null argument");
+  if (!c->grad_valid) return fail(LBM_ERR_STATE, "no adjoint window computed");
+  if (n != c->n * c->q) return fail(LBM_ERR_ARG, "state length %zu, expected %zu", n, c->n * c->q);
+  // a^{n0-1} = S^T b^{n0}: pull into the other adjoint buffer, widen to FP64.
+  c->impl->pull(c->adjbuf(c->bout_last), c->adjbuf(c->bout_last ^ 1));
+  c->impl->to_double(c->adjbuf(c->bout_last ^ 1));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(a, c->at(c->lay.stage), n * 8, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_advance(lbm_ctx* c, int32_t nsteps) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+  cudaEvent_t e = c->begin();
+  for (int j = 0; j < nsteps; ++j) {
+    c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), 0);
+    c->cur ^= 1;
+  }
+  c->end(e, 0, nsteps, int64_t(nsteps) * int64_t(c->n));
+  CUDA_TRY(cudaGetLastError());
+  c->steps += nsteps;
+  c->window_valid = false;
+  c->grad_valid = false;
+  LBM_TRY(check_flags(c, 0, LBM_ERR_NONFINITE, "a non-positive density or non-finite value appeared"));
+  c->harvest();
+  return LBM_OK;
+}
+
+lbm_status lbm_set_timing(lbm_ctx* c, int32_t enable) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  c->timing = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_timing(lbm_ctx* c, lbm_timing* out) {
+  if (!c || !out) return fail(LBM_ERR_ARG, "null argument");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->harvest();
+  *out = c->tm;
+  c->tm = lbm_timing{};
+  return LBM_OK;
+}
+
+lbm_status lbm_get_counters(lbm_ctx* c, int64_t* steps, int64_t* windows) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (steps) *steps = c->steps;
+  if (windows) *windows = c->windows;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+"""The C ABI without a GPU: the library loads, exports every declared entry
+point, and rejects invalid configurations on the host before any CUDA call."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2608_19617_b300 import binding as B, build
+from paper_2608_19617_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return B.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbmadj.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_the_c_compiler(lib, tmp_path):
+    """Offsets of every field of lbm_config / lbm_timing as gcc lays them out
+    from the header equal the ctypes mirror's."""
+    fields = [f for f, _ in B.LbmConfig._fields_]
+    tfields = [f for f, _ in B.LbmTiming._fields_]
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbmadj.h"', "int main(void){"]
+    prog.append('printf("%zu\\n", sizeof(lbm_config));')
+    prog += [f'printf("%zu\\n", offsetof(lbm_config, {f}));' for f in fields]
+    prog.append('printf("%zu\\n", sizeof(lbm_timing));')
+    prog += [f'printf("%zu\\n", offsetof(lbm_timing, {f}));' for f in tfields]
+    prog.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(B.LbmConfig)] + [getattr(B.LbmConfig, f).offset for f in fields]
+    want += [ctypes.sizeof(B.LbmTiming)] + [getattr(B.LbmTiming, f).offset for f in tfields]
+    assert got == want
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert B.status_string(s)
+    assert B.status_string(99) == "unknown status"
+
+
+def _cfg(**kw):
+    case = I.small_channel(16, 8)
+    return B.config_from_case(case, **kw)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("tau", 0.5), ("lattice", 7), ("nz", 2), ("window_len", 0), ("sample_every", 3),
+    ("ckpt_every", 7), ("g_max", 1.5), ("precision", 5), ("rho_out", -1.0),
+    ("objective_kind", 9), ("q_interp", 0.0), ("ckpt_format", 3),
+])
+def test_invalid_configs_are_rejected(lib, field, value):
+    cfg = _cfg()
+    setattr(cfg, field, value)
+    with pytest.raises(B.LbmError) as e:
+        B.workspace_size(cfg)
+    assert e.value.status == B.LBM_ERR_ARG
+    assert B.last_error()
+
+
+def test_sixteen_bit_checkpoints_need_fp32(lib):
+    cfg = _cfg(precision=B.LBM_FP64)
+    cfg.ckpt_format = 1
+    with pytest.raises(B.LbmError):
+        B.workspace_size(cfg)
+
+
+def test_bad_box_rejected(lib):
+    cfg = _cfg()
+    cfg.design_box[1] = 99
+    with pytest.raises(B.LbmError):
+        B.workspace_size(cfg)
+
+
+def test_workspace_grows_with_segment_length(lib):
+    a = B.workspace_size(_cfg())
+    cfg = _cfg()
+    cfg.ckpt_every = 10
+    b = B.workspace_size(cfg)
+    cfg.ckpt_every = 1
+    c = B.workspace_size(cfg)
+    assert a > b and c > 0
+
+
+def _create(case, cls=None, **kw):
+    cfg = B.config_from_case(case, **kw)
+    cls = case.node_class.reshape(-1).astype(np.uint8) if cls is None else cls
+    gam = case.gamma.reshape(-1).astype(np.float32)
+    ctx = ctypes.c_void_p()
+    st = B.lib().lbm_create(ctypes.byref(cfg), cls.ctypes.data, gam.ctypes.data, None, None,
+                            None, 0, None, ctypes.byref(ctx))
+    return st
+
+
+def test_create_rejects_bad_node_classes_on_the_host(lib):
+    case = I.small_channel(16, 8)
+    cls = case.node_class.reshape(-1).astype(np.uint8).copy()
+    bad = cls.copy()
+    bad[3 * 16 + 5] = I.WALL            # interior node must be FLUID
+    assert _create(case, bad) == B.LBM_ERR_ARG
+    bad = cls.copy()
+    bad[3 * 16 + 15] = I.INLET          # inlet on the east face
+    assert _create(case, bad) == B.LBM_ERR_ARG
+    bad = cls.copy()
+    bad[0] = I.INLET                    # inlet on a corner
+    assert _create(case, bad) == B.LBM_ERR_ARG
+    bad = cls.copy()
+    bad[3 * 16 + 0] = I.FLUID           # boundary node with unknowns
+    assert _create(case, bad) == B.LBM_ERR_ARG
+    bad = cls.copy()
+    bad[3 * 16 + 0] = 9                 # unknown class
+    assert _create(case, bad) == B.LBM_ERR_ARG
+
+
+def test_create_rejects_a_missing_workspace(lib):
+    case = I.small_channel(16, 8)
+    assert _create(case) == B.LBM_ERR_WORKSPACE
+
+
+def test_pressure_outlet_is_d2q9_only(lib):
+    case = I.small_duct3d(8, 5, 5, outlet=I.OUTLET_P)
+    assert _create(case) == B.LBM_ERR_ARG

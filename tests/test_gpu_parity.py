@@ -1,0 +1,288 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the arithmetic):
+  * FP64 build vs oracle: 1e-12 relative (norm-wise) on states, window means,
+    gradients -- both sides are FP64 and the trajectories are non-chaotic over
+    these horizons, so differences are rounding-order only;
+  * FP32 build after 200 steps: 1e-5 relative (norm-wise) on rho and on u over
+    fluid nodes (gamma < 1/2);
+  * FP32 adjoint over short windows: gradient cosine >= 0.9999 and 1e-3
+    relative norm-wise against the FP64 oracle.
+Sizes span several 128-node row tiles with a ragged tail.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm as O
+from paper_2608_19617_b300 import binding as B
+from paper_2608_19617_b300 import inputs as I
+
+from _util import cosine, f32_inputs, fluid_moments, oracle_advance, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2608_19617_b300 import build
+    build.build()
+    B.lib()
+
+
+FWD_CASES = {
+    "zouhe300x20": lambda: I.small_channel(300, 20, outlet=I.OUTLET_P, profile="parabolic", u_in=0.06,
+                                           tau=0.53, cs_smag=0.12, window_len=20),
+    "zerograd140x13": lambda: I.small_channel(140, 13, outlet=I.OUTLET_ZG, u_in=0.05, tau=0.52,
+                                              window_len=20, obj_kind=I.OBJ_VELOCITY_DEV),
+    "periodic-x131x9": lambda: I.small_channel(131, 9, periodic_x=True, tau=0.55, window_len=20,
+                                               obj_kind=I.OBJ_DRAG, g_max=0.8),
+    "duct3d-150x7x6": lambda: I.small_duct3d(150, 7, 6, tau=0.53, window_len=20),
+    "duct3d-periodicz": lambda: I.small_duct3d(133, 6, 5, tau=0.54, periodic_z=True, window_len=20,
+                                               obj_kind=I.OBJ_DISSIPATION),
+}
+
+
+def _developed(pr, steps):
+    return oracle_advance(pr, pr.initial_state(), steps)
+
+
+@pytest.mark.parametrize("name", list(FWD_CASES))
+def test_forward_fp64_matches_oracle(name):
+    case = f32_inputs(FWD_CASES[name]())
+    pr = O.Problem(case)
+    sol = B.Solver(case, B.LBM_FP64)
+    sol.advance(200)
+    got = sol.get_state()
+    want = oracle_advance(pr, pr.initial_state(), 200)
+    assert rel_err(got, want) < 1e-12
+    assert np.abs(got - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", list(FWD_CASES))
+def test_forward_fp32_within_1e5(name):
+    case = f32_inputs(FWD_CASES[name]())
+    pr = O.Problem(case)
+    sol = B.Solver(case, B.LBM_FP32)
+    sol.advance(200)
+    got = sol.get_state()
+    want = oracle_advance(pr, pr.initial_state(), 200)
+    rg, ug = fluid_moments(pr, got, case)
+    rw, uw = fluid_moments(pr, want, case)
+    assert rel_err(rg, rw) < 1e-5
+    assert rel_err(ug, uw) < 1e-5
+
+
+ADJ_CASES = {
+    "diss-zouhe": lambda: I.small_channel(150, 12, obj_kind=I.OBJ_DISSIPATION, window_len=12,
+                                          outlet=I.OUTLET_P, profile="parabolic", tau=0.53, cs_smag=0.12),
+    "veldev-zg-dw3": lambda: I.small_channel(140, 11, obj_kind=I.OBJ_VELOCITY_DEV, window_len=12,
+                                             outlet=I.OUTLET_ZG, sample_every=3, tau=0.52),
+    "pressure": lambda: I.small_channel(133, 10, obj_kind=I.OBJ_PRESSURE, window_len=10, tau=0.56),
+    "drag-periodic": lambda: I.small_channel(129, 9, obj_kind=I.OBJ_DRAG, window_len=10,
+                                             periodic_x=True, g_max=0.9, monitor_kind=I.MON_OBJECTIVE),
+    "d3q19-pressure": lambda: I.small_duct3d(130, 6, 6, window_len=8, tau=0.53),
+    "d3q19-diss-periodicz": lambda: I.small_duct3d(131, 6, 5, window_len=8, obj_kind=I.OBJ_DISSIPATION,
+                                                   periodic_z=True, tau=0.54),
+}
+
+
+def _gpu_window_and_adjoint(case, precision, p_start, **kw):
+    sol = B.Solver(case, precision, **kw)
+    sol.set_state(p_start)
+    J, M = sol.step_window()
+    Jeff = sol.adjoint_window()
+    grad = sol.design_gradient()
+    a0 = sol.get_adjoint_state()
+    return sol, J, M, Jeff, grad, a0
+
+
+@pytest.mark.parametrize("name", list(ADJ_CASES))
+def test_window_and_adjoint_fp64_match_oracle(name):
+    case = f32_inputs(ADJ_CASES[name]())
+    pr = O.Problem(case)
+    p0 = _developed(pr, 40)
+    _, Jw, Mw, traj = pr.run_window(p0)
+    _, grad_w, a0_w = pr.adjoint_window(traj)
+    sol, J, M, Jeff, grad, a0 = _gpu_window_and_adjoint(case, B.LBM_FP64, p0)
+    assert abs(J - Jw) <= 1e-12 * abs(Jw)
+    assert abs(M - Mw) <= 1e-12 * abs(Mw) + 1e-300
+    assert Jeff == J
+    dbox = np.zeros((case.nz, case.ny, case.nx), bool)
+    x0, x1, y0, y1, z0, z1 = case.design_box
+    dbox[z0:z1, y0:y1, x0:x1] = True
+    dbox = dbox.reshape(-1)
+    assert rel_err(grad[dbox], grad_w[dbox]) < 1e-11
+    assert np.all(grad[~dbox] == 0)
+    assert rel_err(a0, a0_w) < 1e-11
+
+
+@pytest.mark.parametrize("name", list(ADJ_CASES))
+def test_window_and_adjoint_fp32_match_oracle(name):
+    case = f32_inputs(ADJ_CASES[name]())
+    pr = O.Problem(case)
+    p0 = _developed(pr, 40)
+    _, Jw, Mw, traj = pr.run_window(p0)
+    _, grad_w, a0_w = pr.adjoint_window(traj)
+    sol, J, M, Jeff, grad, a0 = _gpu_window_and_adjoint(case, B.LBM_FP32, p0)
+    assert abs(J - Jw) <= 1e-4 * abs(Jw)
+    x0, x1, y0, y1, z0, z1 = case.design_box
+    m = np.zeros((case.nz, case.ny, case.nx), bool)
+    m[z0:z1, y0:y1, x0:x1] = True
+    m = m.reshape(-1)
+    assert cosine(grad[m], grad_w[m]) > 0.9999
+    assert rel_err(grad[m], grad_w[m]) < 1e-3
+    assert cosine(a0, a0_w) > 0.9999
+
+
+def test_recompute_from_checkpoints_is_bitwise():
+    """Segments of K < |W| recompute the same trajectory: identical gradient."""
+    case = f32_inputs(I.small_channel(150, 12, window_len=24, outlet=I.OUTLET_P, tau=0.53))
+    pr = O.Problem(case)
+    p0 = _developed(pr, 30)
+    grads = []
+    for K in (24, 6, 1):
+        sol = B.Solver(case.replace(ckpt_every=K), B.LBM_FP32)
+        sol.set_state(p0)
+        sol.step_window()
+        sol.adjoint_window()
+        grads.append(sol.design_gradient())
+    assert np.array_equal(grads[0], grads[1]) and np.array_equal(grads[0], grads[2])
+
+
+@pytest.mark.parametrize("fmt", [I.CKPT_FP16, I.CKPT_BF16])
+def test_sixteen_bit_checkpoints_keep_the_gradient(fmt):
+    case = f32_inputs(I.small_channel(200, 16, window_len=40, outlet=I.OUTLET_P, tau=0.53))
+    pr = O.Problem(case)
+    p0 = _developed(pr, 60)
+    out = {}
+    for f in (I.CKPT_NATIVE, fmt):
+        sol = B.Solver(case.replace(ckpt_every=8, ckpt_format=f), B.LBM_FP32)
+        sol.set_state(p0)
+        J, _ = sol.step_window()
+        sol.adjoint_window()
+        out[f] = (J, sol.design_gradient())
+    assert out[fmt][0] == out[I.CKPT_NATIVE][0]     # the forward is not touched
+    assert cosine(out[fmt][1], out[I.CKPT_NATIVE][1]) > 0.999
+
+
+def test_window_sequence_and_criterion_fp64():
+    """Consecutive windows: means and the ratio of Eq. 26 against the oracle."""
+    case = f32_inputs(I.small_channel(140, 12, window_len=15, outlet=I.OUTLET_P, tau=0.53))
+    pr = O.Problem(case)
+    rec = pr.run_until_converged(max_windows=4)
+    sol = B.Solver(case, B.LBM_FP64)
+    for i, r in enumerate(rec):
+        J, M = sol.step_window()
+        conv, ratio = sol.window_converged()
+        assert abs(J - r["J"]) <= 1e-12 * abs(r["J"])
+        assert abs(M - r["M"]) <= 1e-12 * abs(r["M"])
+        if i == 0:
+            assert ratio == float("inf") and not conv
+        else:
+            assert abs(ratio - r["ratio"]) <= 1e-9 * abs(r["ratio"]) + 1e-15
+            assert conv == r["converged"]
+
+
+def test_error_paths():
+    case = f32_inputs(I.small_channel(64, 10, window_len=10))
+    sol = B.Solver(case, B.LBM_FP32)
+    with pytest.raises(B.LbmError) as e:
+        sol.adjoint_window()
+    assert e.value.status == B.LBM_ERR_STATE
+    with pytest.raises(B.LbmError) as e:
+        sol.design_gradient()
+    assert e.value.status == B.LBM_ERR_STATE
+    p = sol.get_state()
+    bad = p.copy()
+    bad[0, 5] = np.nan
+    with pytest.raises(B.LbmError) as e:
+        sol.set_state(bad)
+    assert e.value.status == B.LBM_ERR_ARG
+    neg = p.copy()
+    neg[:, 3 * 64 + 20] = -0.2                       # a node with negative density
+    sol.set_state(neg)
+    with pytest.raises(B.LbmError) as e:
+        sol.step_window()
+    assert e.value.status == B.LBM_ERR_NONFINITE
+    sol.set_state(p)                                 # recovers
+    sol.step_window()
+    with pytest.raises(B.LbmError) as e:
+        sol.set_design(np.full(case.n, 1.5, np.float32))
+    assert e.value.status == B.LBM_ERR_ARG
+
+
+def test_state_round_trip_and_counters():
+    case = f32_inputs(I.small_duct3d(20, 6, 6))
+    sol = B.Solver(case, B.LBM_FP64)
+    rng = np.random.default_rng(0)
+    lat = O.Lattice(19)
+    p = lat.w[:, None] * (1 + 0.01 * rng.standard_normal((19, case.n)))
+    sol.set_state(p)
+    assert np.abs(sol.get_state() - p).max() < 1e-16
+    sol.advance(3)
+    assert sol.counters() == (3, 0)
+
+
+def test_device_buffers_and_autograd():
+    """Design and gradient through device pointers, and the autograd function."""
+    import torch
+    from paper_2608_19617_b300.autograd import window_objective
+    case = f32_inputs(I.small_channel(140, 12, window_len=12, outlet=I.OUTLET_P, tau=0.53))
+    pr = O.Problem(case)
+    sol = B.Solver(case, B.LBM_FP64)
+    gam = torch.tensor(case.gamma.reshape(-1), dtype=torch.float32, device="cuda", requires_grad=True)
+    J = window_objective(gam, sol, 2)
+    J.backward()
+    rec = pr.run_until_converged(max_windows=2)
+    traj = pr.run_window(rec[-1]["p_start"])[3]
+    _, grad_w, _ = pr.adjoint_window(traj)
+    assert abs(J.item() - rec[-1]["J"]) <= 1e-12 * abs(rec[-1]["J"])
+    x0, x1, y0, y1, _, _ = case.design_box
+    m = np.zeros((case.ny, case.nx), bool)
+    m[y0:y1, x0:x1] = True
+    g = gam.grad.detach().cpu().numpy().astype(np.float64)
+    assert rel_err(g[m.reshape(-1)], grad_w[m.reshape(-1)]) < 1e-6   # float32 gradient tensor
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads in the benchmark's launch configuration.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["wake1024x256", "step2048x512"])
+def test_full_size_one_step_against_oracle(name):
+    """After a spin-up on the GPU, one more GPU step equals the oracle's step
+    from the same field, element by element (FP32 vs FP64)."""
+    case = f32_inputs(I.WORKLOADS[name]())
+    sol = B.Solver(case, B.LBM_FP32)
+    sol.advance(300)
+    p = sol.get_state()
+    sol.advance(1)
+    got = sol.get_state()
+    pr = O.Problem(case)
+    want = oracle_advance(pr, p, 1)
+    assert np.abs(got - want).max() < 2e-6
+
+
+def test_full_size_short_window_adjoint_against_oracle():
+    """A two-step window at the wake workload's full size: gradient and start
+    adjoint against the oracle (FP32 vs FP64)."""
+    import numpy as np
+    base = I.WORKLOADS["wake1024x256"]()
+    # drag of the partial bounce-back force summed over the whole lattice, so
+    # that a two-step adjoint reaches every design node
+    case = f32_inputs(base.replace(obj_kind=I.OBJ_DRAG, obj_weights=np.ones_like(base.obj_weights),
+                                   window_len=2, ckpt_every=2))
+    sol = B.Solver(case, B.LBM_FP32)
+    sol.advance(200)
+    p = sol.get_state()
+    sol.step_window()
+    sol.adjoint_window()
+    grad = sol.design_gradient()
+    pr = O.Problem(case)
+    _, _, _, traj = pr.run_window(p)
+    _, grad_w, _ = pr.adjoint_window(traj)
+    m = grad_w != 0
+    assert m.sum() > 0
+    assert cosine(grad[m], grad_w[m]) > 0.9999

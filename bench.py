@@ -29,6 +29,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The CPU oracle is timed on one thread: pin every BLAS / OpenMP pool to one
+# thread before numpy loads, so that the reported core count is exact.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 METRIC = "forward & adjoint MLUPS and % HBM roofline, FP32/mixed vs FP64 at stated error"
 WORKLOAD = "wake1024x256"
@@ -45,7 +49,15 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--window-len", type=int, default=0, help="override |W| (profiling runs)")
+    ap.add_argument("--ckpt-every", type=int, default=0, help="override K (profiling runs)")
+    ap.add_argument("--spinup-windows", type=int, default=4)
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling run: no CPU baseline, no FP64 check, no e2e pass")
+    a = ap.parse_args()
+    if a.quick:
+        a.no_cpu_baseline = a.no_fp64_check = True
+    return a
 
 
 def dist_env():
@@ -158,12 +170,16 @@ def peaks():
 def oracle_sample(case, fwd_steps, seconds_hint=None):
     """Time the FP64 oracle on a bounded sample of the workload: a window of
     ``fwd_steps`` steps from a developed-looking start, then its adjoint."""
-    import numpy as np
-    from threadpoolctl import threadpool_limits
+    import contextlib
 
     from oracle import lbm as O
+    try:
+        from threadpoolctl import threadpool_limits
+        limit = threadpool_limits(limits=1)
+    except ImportError:
+        limit = contextlib.nullcontext()
     c = case.replace(window_len=fwd_steps, ckpt_every=fwd_steps, sample_every=1)
-    with threadpool_limits(limits=1):
+    with limit:
         pr = O.Problem(c)
         p0 = pr.initial_state()
         t0 = time.perf_counter()
@@ -248,8 +264,8 @@ def run_ours(args, case, rank, world, local):
         sol.adjoint_window()
         sol.design_gradient(grad_dev)
 
-    # spin-up so that the timed windows see a developed wake
-    sol.advance(4 * W)
+    # spin-up so that the timed windows see a developed flow
+    sol.advance(args.spinup_windows * W)
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
@@ -279,19 +295,21 @@ def run_ours(args, case, rank, world, local):
     value = world * args.steps * lus_step / (ms / 1e3) / 1e6
 
     # e2e: host design in, host gradient out, through the C ABI, per step.
-    gam_host = torch.from_numpy(case.gamma.reshape(-1).astype(np.float32)).pin_memory()
-    grad_host = torch.empty(n, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sol.set_design(gam_host)
-        sol.step_window()
-        sol.window_converged()
-        sol.adjoint_window()
-        sol.design_gradient(grad_host)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * args.steps * lus_step / e2e_s / 1e6
+    e2e_value = None
+    if not args.quick:
+        gam_host = torch.from_numpy(case.gamma.reshape(-1).astype(np.float32)).pin_memory()
+        grad_host = torch.empty(n, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sol.set_design(gam_host)
+            sol.step_window()
+            sol.window_converged()
+            sol.adjoint_window()
+            sol.design_gradient(grad_host)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_value = world * args.steps * lus_step / e2e_s / 1e6
 
     if rank != 0:
         return 0
@@ -343,13 +361,14 @@ def run_ours(args, case, rank, world, local):
                           f"lattice plus its adjoint ({r['lattice_updates']} lattice updates, {r['seconds']:.1f} s)"),
                "cpu": cpu_model()}
 
-    launches_per_step = W + 1 + (W - S) + W + 1
+    launches_per_step = W + 1 + (W - S) + W + 1 + (2 * S if case.ckpt_format else 0)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded inputs shaped like the paper's cylinder wake)",
-        "config": {"workload": case.name, "lattice": "D2Q9", "nx": case.nx, "ny": case.ny,
+        "config": {"workload": case.name, "lattice": f"D{2 if case.lattice == 9 else 3}Q{case.lattice}",
+                   "nx": case.nx, "ny": case.ny, "nz": case.nz,
                    "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
                    "ckpt_format": ["fp32", "fp16", "bf16"][case.ckpt_format], "tau": case.tau,
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
@@ -360,7 +379,8 @@ def run_ours(args, case, rank, world, local):
             ((timing["adjoint"]["ms"] + timing["recompute"]["ms"] + timing["checkpoint"]["ms"]) / 1e3),
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n},
+        "e2e": (None if e2e_value is None else
+                {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n}),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
         "error": err,
@@ -374,6 +394,9 @@ def main():
     rank, world, local = dist_env()
     from paper_2608_19617_b300 import inputs as I
     case = I.WORKLOADS[args.workload]()
+    if args.window_len or args.ckpt_every:
+        wl = args.window_len or case.window_len
+        case = case.replace(window_len=wl, ckpt_every=args.ckpt_every or wl)
     if args.impl == "reference":
         rc = run_reference(args, case, rank, world)
         return rc

@@ -33,3 +33,15 @@ def fluid_moments(pr, p, case):
     rho, u = O.moments_of(pr.lat, pr.stream(p))
     fluid = case.gamma.reshape(-1) < 0.5
     return rho[fluid], u[:, fluid]
+
+
+def initial_flow(pr, amp=0.04):
+    """A smooth moving equilibrium (rho = 1): u_x = amp (1 + sin), u_y = amp/4 sin.
+    Gives every case -- periodic ones included -- a nontrivial flow."""
+    n = pr.n
+    i = np.arange(n)
+    x, y = i % pr.nx, (i // pr.nx) % pr.ny
+    u = np.zeros((pr.lat.d, n))
+    u[0] = amp * (1.0 + 0.5 * np.sin(2 * np.pi * y / pr.ny))
+    u[1] = 0.25 * amp * np.sin(2 * np.pi * x / pr.nx)
+    return O.equilibrium(pr.lat, np.ones(n), u)

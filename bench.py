@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--window-len", type=int, default=0, help="override |W| (profiling runs)")
     ap.add_argument("--ckpt-every", type=int, default=0, help="override K (profiling runs)")
     ap.add_argument("--spinup-windows", type=int, default=4)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: no CPU baseline, no FP64 check, no e2e pass")
     a = ap.parse_args()
@@ -250,8 +251,9 @@ def run_ours(args, case, rank, world, local):
     B.lib()
 
     stream = torch.cuda.Stream()
+    prec = B.LBM_FP64 if args.precision == "fp64" else B.LBM_FP32
     with torch.cuda.stream(stream):
-        sol = B.Solver(case, B.LBM_FP32, stream=stream)
+        sol = B.Solver(case, prec, stream=stream)
     n = case.n
     W, K = case.window_len, case.ckpt_every
     S = W // K
@@ -321,7 +323,7 @@ def run_ours(args, case, rank, world, local):
         t = timing[ph]
         if t["launches"]:
             avg_ms = t["ms"] / t["launches"]
-            bpl = bytes_per_lu(case, ph) * n
+            bpl = bytes_per_lu(case, ph, rs=8 if prec == B.LBM_FP64 else 4) * n
             phase_rows[ph] = {"launches": t["launches"], "ms": t["ms"], "avg_launch_us": 1e3 * avg_ms,
                               "bytes_per_launch": bpl, "gbs": bpl / (avg_ms / 1e3) / 1e9}
     dom = max(phase_rows, key=lambda p: phase_rows[p]["ms"])
@@ -330,12 +332,12 @@ def run_ours(args, case, rank, world, local):
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": measured_traffic(kname, case.name), "kernel": kname, "phase": dom,
             "peak_kind": f"{pk_kind} hbm_gbs (copy)",
-            "bytes_per_lu": bytes_per_lu(case, dom), "phases": phase_rows}
+            "bytes_per_lu": bytes_per_lu(case, dom, rs=8 if prec == B.LBM_FP64 else 4), "phases": phase_rows}
 
     # Accuracy beside the number: the FP32 window and adjoint against the FP64
     # GPU path from the same start field.
     err = None
-    if not args.no_fp64_check:
+    if not args.no_fp64_check and prec == B.LBM_FP32:
         p = sol.get_state()
         with torch.cuda.stream(stream):
             ref = B.Solver(case, B.LBM_FP64, stream=stream)
@@ -365,7 +367,7 @@ def run_ours(args, case, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == B.LBM_FP64 else "f32",
         "data": "synthetic (seeded inputs shaped like the paper's cylinder wake)",
         "config": {"workload": case.name, "lattice": f"D{2 if case.lattice == 9 else 3}Q{case.lattice}",
                    "nx": case.nx, "ny": case.ny, "nz": case.nz,

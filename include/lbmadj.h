@@ -184,6 +184,13 @@ lbm_status lbm_advance(lbm_ctx* ctx, int32_t nsteps);
 lbm_status lbm_set_timing(lbm_ctx* ctx, int32_t enable);
 lbm_status lbm_get_timing(lbm_ctx* ctx, lbm_timing* out);
 
+/* Replay each window and each adjoint sweep as one CUDA graph (1, the
+ * default) or launch every kernel individually (0).  Results are identical;
+ * graphs remove the per-launch host overhead that dominates small lattices.
+ * Graphs are captured on first use on a private stream and launched into the
+ * context's stream. */
+lbm_status lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
+
 /* Total steps advanced and windows completed since lbm_create. */
 lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);
 

@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
         "lbm_set_timing": (st, [c_void_p, c_int32]),
         "lbm_get_timing": (st, [c_void_p, POINTER(LbmTiming)]),
         "lbm_get_counters": (st, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
+        "lbm_set_graphs": (st, [c_void_p, c_int32]),
         "lbm_status_string": (ctypes.c_char_p, [c_int32]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_destroy": (None, [c_void_p]),
@@ -219,6 +220,9 @@ class Solver:
         check(lib().lbm_get_timing(self.ctx, byref(t)), "lbm_get_timing")
         return {PHASES[k]: dict(ms=t.ms[k], launches=t.launches[k], lattice_updates=t.lattice_updates[k])
                 for k in range(NUM_PHASES)}
+
+    def set_graphs(self, enable: bool):
+        check(lib().lbm_set_graphs(self.ctx, int(bool(enable))), "lbm_set_graphs")
 
     def counters(self):
         s, w = c_int64(), c_int64()

@@ -16,6 +16,19 @@
 // (Eq. 36), recomputes f^n from p^{n-1}, applies the transposed local
 // Jacobian in moment space (Eq. 35) and the transposed boundary rule
 // (Eqs. 37-39), and stores the result at its own node.
+//
+// Two identities keep the per-direction work small.  The regularized
+// collision (Eq. 16) only carries Hermite moments up to second order, so
+// h_a = w_a (H0 + H1.c_a + c_a.H2.c_a), and the partial bounce-back of Eq. 23,
+// p = (1-g) h + g h_abar, keeps the even part and scales the odd part H1 by
+// (1 - 2g).  Hence p~_a = w_a (A + B.c_a + c_a.T.c_a) with one scalar, one
+// vector and one symmetric tensor per node; the adjoint of the blend scales
+// the first adjoint moment by (1 - 2g); and the sensitivity term of Eq. 40,
+// sum_a a_a (h_abar - h_a), equals -6 m . sum_a w_a c_a a_a.
+//
+// Boundary nodes take out-of-line slow paths so that the interior code stays
+// small (instruction-cache pressure), and indices are 32-bit (Q N < 2^31 is
+// checked on the host).
 #pragma once
 
 #include <cstdint>
@@ -35,8 +48,8 @@ constexpr int kBlock = 128;   // threads per block (one row segment of 128 nodes
 struct Geo {
   int nx, ny, nz;
   int px, py, pz;             // periodic flags
-  long long n;                // nx*ny*nz
-  long long sy, sz;           // strides of y and z
+  unsigned n;                 // nx*ny*nz
+  unsigned sy, sz;            // strides of y and z
 };
 
 template <class R>
@@ -54,14 +67,10 @@ struct Obj {
   R uref[3];
   int box[6];            // weights read only inside
   R ws;                  // sampling weight dW/|W| (adjoint source scale)
-  double mon_scale;      // 1 / (rho0 U^2 L / 2) for the drag coefficient
-  double jconst;         // constant part of j (cs^2 * sum of weights for PRESSURE)
 };
 
-// Window accumulators (FP64, compensated) and the window-end results.
+// Window-end results.
 struct WindowAcc {
-  double jsum, jcomp, msum, mcomp;
-  long long count;
   double jmean, mmean, mprev, ratio;
   int has_prev, converged, nonfinite, pad;
 };
@@ -77,12 +86,12 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
 
 // Neighbour (x+dx, y+dy, z+dz) with periodic wrap; false if outside.
 __device__ __forceinline__ bool neighbour(const Geo& g, int x, int y, int z, int dx, int dy, int dz,
-                                          long long& j) {
+                                          unsigned& j) {
   int X = x + dx, Y = y + dy, Z = z + dz;
   if (X < 0 || X >= g.nx) { if (!g.px) return false; X = (X + g.nx) % g.nx; }
   if (Y < 0 || Y >= g.ny) { if (!g.py) return false; Y = (Y + g.ny) % g.ny; }
   if (Z < 0 || Z >= g.nz) { if (!g.pz) return false; Z = (Z + g.nz) % g.nz; }
-  j = X + Y * g.sy + Z * g.sz;
+  j = unsigned(X) + unsigned(Y) * g.sy + unsigned(Z) * g.sz;
   return true;
 }
 
@@ -94,26 +103,21 @@ __device__ __forceinline__ bool on_face(const Geo& g, int x, int y, int z) {
 }
 
 template <class L>
-__device__ __forceinline__ long long offset(const Geo& g, int a) {
-  return L::cx(a) + L::cy(a) * g.sy + L::cz(a) * g.sz;
+__device__ __forceinline__ int offset(const Geo& g, int a) {
+  return L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz);
 }
 
 // ---------------------------------------------------------------------------
-// Streaming with boundary completion: f^n at node (x,y,z) from p^{n-1}.
+// Streaming with boundary completion on a domain face: f^n at node (x,y,z)
+// from p^{n-1}.  Out of line: only face nodes come here.
 // ---------------------------------------------------------------------------
 template <class L, class R>
-__device__ __forceinline__ void gather(const R* __restrict__ P, const Geo& g, int x, int y, int z,
-                                       long long i, bool face, uint8_t cls, R u0, R rho_out,
-                                       R (&f)[L::Q], unsigned& unk) {
-  unk = 0;
-  if (!face) {
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = P[a * g.n + i - offset<L>(g, a)];
-    return;
-  }
+__device__ __noinline__ unsigned gather_face(const R* __restrict__ P, const Geo& g, int x, int y, int z,
+                                             uint8_t cls, R u0, R rho_out, R* f) {
+  unsigned unk = 0;
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
-    long long j;
+    unsigned j;
     if (neighbour(g, x, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j)) {
       f[a] = P[a * g.n + j];
     } else {
@@ -121,7 +125,7 @@ __device__ __forceinline__ void gather(const R* __restrict__ P, const Geo& g, in
       unk |= 1u << a;
     }
   }
-  if (!unk) return;
+  if (!unk) return 0;
   if (cls == WALL) {
     // Eq. 19: an unknown population takes its opposite's value; a link whose
     // opposite is unknown too stays at its rest weight (shifted value 0).
@@ -157,12 +161,28 @@ __device__ __forceinline__ void gather(const R* __restrict__ P, const Geo& g, in
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
       if (unk & (1u << a)) {
-        long long j = 0;
+        unsigned j = 0;
         neighbour(g, xn, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j);   // inside (validated on the host)
         f[a] = P[a * g.n + j];
       }
     }
   }
+  return unk;
+}
+
+template <class L, class R>
+__device__ __forceinline__ unsigned gather(const R* __restrict__ P, const Geo& g, int x, int y, int z, unsigned i,
+                                           bool face, uint8_t cls, R u0, R rho_out, R (&f)[L::Q]) {
+  if (!face) {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) f[a] = P[a * g.n + i - offset<L>(g, a)];
+    return 0;
+  }
+  R t[L::Q];
+  const unsigned unk = gather_face<L, R>(P, g, x, y, z, cls, u0, rho_out, t);
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) f[a] = t[a];
+  return unk;
 }
 
 // ---------------------------------------------------------------------------
@@ -179,36 +199,48 @@ struct Mom {
   R te, om;                // tau_eff (Eq. 14), 1 - 1/tau_eff
 };
 
-template <class L, class R>
-__device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<L, R>& M) {
+// Zeroth, first and second moments of a population-shaped array, each
+// weighted by wt(a) (1 for f, w_a for adjoints).
+template <class L, class R, bool W>
+__device__ __forceinline__ void raw_moments(const R (&f)[L::Q], R& m0, R (&m1)[3], R (&m2)[6]) {
   R rt = 0, mx = 0, my = 0, mz = 0, xx = 0, yy = 0, zz = 0, xy = 0, xz = 0, yz = 0;
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
-    const R v = f[a];
+    const R v = W ? R(L::w(a)) * f[a] : f[a];
+    const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
     rt += v;
-    if (L::cx(a)) mx += L::cx(a) * v;
-    if (L::cy(a)) my += L::cy(a) * v;
-    if (L::cz(a)) mz += L::cz(a) * v;
-    if (L::cx(a)) xx += v;
-    if (L::cy(a)) yy += v;
-    if (L::cz(a)) zz += v;
-    if (L::cx(a) * L::cy(a)) xy += (L::cx(a) * L::cy(a)) * v;
-    if (L::cx(a) * L::cz(a)) xz += (L::cx(a) * L::cz(a)) * v;
-    if (L::cy(a) * L::cz(a)) yz += (L::cy(a) * L::cz(a)) * v;
+    if (cx > 0) mx += v; else if (cx < 0) mx -= v;
+    if (cy > 0) my += v; else if (cy < 0) my -= v;
+    if (cz > 0) mz += v; else if (cz < 0) mz -= v;
+    if (cx) xx += v;
+    if (cy) yy += v;
+    if (cz) zz += v;
+    if (cx * cy > 0) xy += v; else if (cx * cy < 0) xy -= v;
+    if (cx * cz > 0) xz += v; else if (cx * cz < 0) xz -= v;
+    if (cy * cz > 0) yz += v; else if (cy * cz < 0) yz -= v;
   }
+  m0 = rt;
+  m1[0] = mx; m1[1] = my; m1[2] = mz;
+  m2[0] = xx; m2[1] = yy; m2[2] = zz; m2[3] = xy; m2[4] = xz; m2[5] = yz;
+}
+
+template <class L, class R>
+__device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<L, R>& M) {
+  R rt, m[3], m2[6];
+  raw_moments<L, R, false>(f, rt, m, m2);
   M.rt = rt;
   M.rho = R(1) + rt;
   M.inv = R(1) / M.rho;
-  M.m[0] = mx; M.m[1] = my; M.m[2] = mz;
-  M.u[0] = mx * M.inv; M.u[1] = my * M.inv; M.u[2] = mz * M.inv;
+  M.m[0] = m[0]; M.m[1] = m[1]; M.m[2] = L::D == 3 ? m[2] : R(0);
+  M.u[0] = m[0] * M.inv; M.u[1] = m[1] * M.inv; M.u[2] = M.m[2] * M.inv;
   // Pi = M2 - rho cs^2 I - m m^T / rho; with shifted moments M2~ = M2 - cs^2 I.
   const R c = cs2<R>();
-  M.pi[0] = xx - rt * c - mx * M.u[0];
-  M.pi[1] = yy - rt * c - my * M.u[1];
-  M.pi[2] = (L::D == 3) ? zz - rt * c - mz * M.u[2] : R(0);
-  M.pi[3] = xy - mx * M.u[1];
-  M.pi[4] = (L::D == 3) ? xz - mx * M.u[2] : R(0);
-  M.pi[5] = (L::D == 3) ? yz - my * M.u[2] : R(0);
+  M.pi[0] = m2[0] - rt * c - m[0] * M.u[0];
+  M.pi[1] = m2[1] - rt * c - m[1] * M.u[1];
+  M.pi[2] = (L::D == 3) ? m2[2] - rt * c - M.m[2] * M.u[2] : R(0);
+  M.pi[3] = m2[3] - m[0] * M.u[1];
+  M.pi[4] = (L::D == 3) ? m2[4] - m[0] * M.u[2] : R(0);
+  M.pi[5] = (L::D == 3) ? m2[5] - m[1] * M.u[2] : R(0);
   M.pp = M.pi[0] * M.pi[0] + M.pi[1] * M.pi[1] + M.pi[2] * M.pi[2] +
          R(2) * (M.pi[3] * M.pi[3] + M.pi[4] * M.pi[4] + M.pi[5] * M.pi[5]);
   M.pn = sqrt(R(2) * M.pp);
@@ -218,26 +250,50 @@ __device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, M
   M.om = R(1) - R(1) / M.te;
 }
 
-// h~_a = f^eq_a - w_a + (1 - 1/tau_eff) w_a/(2 cs^4) (c_a c_a - cs^2 I) : Pi   (Eq. 16)
+// Value at direction a of w_a (s0 + s1.c_a + c_a.S2.c_a), S2 symmetric with
+// entries (xx, yy, zz, xy, xz, yz).
 template <class L, class R>
-__device__ __forceinline__ R regularized(const Mom<L, R>& M, int a) {
+__device__ __forceinline__ R quad_form(int a, R s0, const R (&s1)[3], const R (&s2)[6]) {
   const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-  const R cu = cx * M.u[0] + cy * M.u[1] + cz * M.u[2];
-  const R uu = M.u[0] * M.u[0] + M.u[1] * M.u[1] + M.u[2] * M.u[2];
-  const R w = R(L::w(a));
-  const R feq = w * (M.rt + M.rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+  R v = s0;
+  if (cx) v += cx > 0 ? s1[0] : -s1[0];
+  if (cy) v += cy > 0 ? s1[1] : -s1[1];
+  if (cz) v += cz > 0 ? s1[2] : -s1[2];
+  if (cx) v += s2[0];
+  if (cy) v += s2[1];
+  if (cz) v += s2[2];
+  if (cx * cy) v += cx * cy > 0 ? R(2) * s2[3] : R(-2) * s2[3];
+  if (cx * cz) v += cx * cz > 0 ? R(2) * s2[4] : R(-2) * s2[4];
+  if (cy * cz) v += cy * cz > 0 ? R(2) * s2[5] : R(-2) * s2[5];
+  return v;
+}
+
+// Blended post-collision field (Eqs. 16 and 23):
+//   h~_a = f^eq_a - w_a + (1 - 1/tau_eff) w_a/(2 cs^4) (c_a c_a - cs^2 I) : Pi
+//        = w_a (A + 3 m.c_a + c_a.T.c_a),
+//   A = rho - 1 - 1.5 m.u - 1.5 om tr(Pi),  T = 4.5 (m u^T + om Pi),
+// and the blend scales the odd part: p~_a = w_a (A + 3 (1 - 2g) m.c_a + c_a.T.c_a).
+template <class L, class R>
+__device__ __forceinline__ void post_collision(const Mom<L, R>& M, R g, R& A, R (&B)[3], R (&T)[6]) {
   const R tr = M.pi[0] + M.pi[1] + M.pi[2];
-  const R qpi = R(cx * cx) * M.pi[0] + R(cy * cy) * M.pi[1] + R(cz * cz) * M.pi[2] +
-                R(2 * cx * cy) * M.pi[3] + R(2 * cx * cz) * M.pi[4] + R(2 * cy * cz) * M.pi[5] -
-                cs2<R>() * tr;
-  return feq + M.om * R(4.5) * w * qpi;
+  A = M.rt - R(1.5) * (M.m[0] * M.u[0] + M.m[1] * M.u[1] + M.m[2] * M.u[2]) - R(1.5) * M.om * tr;
+  const R b = R(3) * (R(1) - R(2) * g);
+  B[0] = b * M.m[0]; B[1] = b * M.m[1]; B[2] = b * M.m[2];
+  const R k = R(4.5);
+  T[0] = k * (M.m[0] * M.u[0] + M.om * M.pi[0]);
+  T[1] = k * (M.m[1] * M.u[1] + M.om * M.pi[1]);
+  T[2] = k * (M.m[2] * M.u[2] + M.om * M.pi[2]);
+  T[3] = k * (M.m[0] * M.u[1] + M.om * M.pi[3]);
+  T[4] = k * (M.m[0] * M.u[2] + M.om * M.pi[4]);
+  T[5] = k * (M.m[1] * M.u[2] + M.om * M.pi[5]);
 }
 
 // ---------------------------------------------------------------------------
-// Block reduction of two FP64 values; result in thread 0.
+// Block reduction of two values in the working precision; result in thread 0.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kBlock / 32], sb[kBlock / 32];
+template <class R>
+__device__ __forceinline__ void block_sum2(R& a, R& b) {
+  __shared__ R sa[kBlock / 32], sb[kBlock / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
@@ -246,50 +302,24 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) { sa[warp] = a; sb[warp] = b; }
   __syncthreads();
-  if (warp == 0) {
-    a = lane < kBlock / 32 ? sa[lane] : 0.0;
-    b = lane < kBlock / 32 ? sb[lane] : 0.0;
+  if (threadIdx.x == 0) {
+    a = sa[0];
+    b = sb[0];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-    }
+    for (int k = 1; k < kBlock / 32; ++k) { a += sa[k]; b += sb[k]; }
   }
-  __syncthreads();
 }
 
-// Per-block partials, then the last block to finish sums them in a fixed
-// order (deterministic) with compensation and adds the sample to the window.
-__device__ __forceinline__ void sample_commit(double bj, double bm, double* partials,
-                                              unsigned* counter, WindowAcc* acc, double jconst,
-                                              double mon_scale, int mon_kind) {
-  __shared__ bool last;
-  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+// Each block keeps its own compensated FP64 window sums (j and the monitor) in
+// blk[4 b .. 4 b + 3]; thread 0 adds the block's sample.  No atomics, no
+// cross-block step: the window-end kernel reduces the blocks in a fixed order.
+__device__ __forceinline__ void sample_commit(double bj, double bm, double* blk) {
   if (threadIdx.x == 0) {
-    partials[2 * bid] = bj;
-    partials[2 * bid + 1] = bm;
-    __threadfence();
-    last = atomicAdd(counter, 1u) == nb - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double sj = 0, cj = 0, sm = 0, cm = 0;
-  const volatile double* vp = partials;
-  for (unsigned k = threadIdx.x; k < nb; k += blockDim.x) {
-    neumaier(sj, cj, vp[2 * k]);
-    neumaier(sm, cm, vp[2 * k + 1]);
-  }
-  double tj = sj + cj, tm = sm + cm;
-  block_sum2(tj, tm);
-  if (threadIdx.x == 0) {
-    const double j = tj + jconst;
-    const double m = mon_kind == MON_DRAG ? tm * mon_scale : j;
-    neumaier(acc->jsum, acc->jcomp, j);
-    neumaier(acc->msum, acc->mcomp, m);
-    acc->count += 1;
-    *counter = 0;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    double4 a = reinterpret_cast<double4*>(blk)[bid];
+    neumaier(a.x, a.y, bj);
+    neumaier(a.z, a.w, bm);
+    reinterpret_cast<double4*>(blk)[bid] = a;
   }
 }
 
@@ -308,9 +338,7 @@ struct FwdArgs {
   Phys<R> ph;
   Obj<R> obj;
   int sample;                    // 1 at a sampling instant
-  double* partials;
-  unsigned* counter;
-  WindowAcc* acc;
+  double* blk;                   // per-block window sums (4 doubles per block)
   int* nonfinite;
 };
 
@@ -322,7 +350,7 @@ __device__ __forceinline__ R local_objective(const Mom<L, R>& M, const Obj<R>& o
       const R dx = M.u[0] - ob.uref[0], dy = M.u[1] - ob.uref[1], dz = M.u[2] - ob.uref[2];
       return dx * dx + dy * dy + (L::D == 3 ? dz * dz : R(0));
     }
-    case OBJ_PRES: return cs2<R>() * M.rt;     // constant cs^2 sum(w) added once per sample
+    case OBJ_PRES: return cs2<R>() * M.rt;     // constant cs^2 sum(w) added at the window end
     default: return R(-2) * gi * M.m[0];       // sum_a c_xa F_a = -2 g m_x
   }
 }
@@ -332,45 +360,67 @@ __global__ void __launch_bounds__(kBlock) fwd_step_kernel(FwdArgs<R> A) {
   const Geo& g = A.geo;
   const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   const bool alive = x < g.nx;
-  double bj = 0.0, bm = 0.0;
+  R bj = 0, bm = 0;
   if (alive) {
-    const long long i = x + y * g.sy + z * g.sz;
+    const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
     const bool face = on_face<L>(g, x, y, z);
     const uint8_t cls = face ? A.cls[i] : uint8_t(FLUID);
     const R u0 = (face && cls == INLET) ? R(A.uin[y + g.ny * z]) : R(0);
     R f[L::Q];
-    unsigned unk;
-    gather<L, R>(A.src, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f, unk);
+    gather<L, R>(A.src, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f);
     Mom<L, R> M;
     moments<L, R>(f, A.ph, M);
     if (!(M.rho > R(0)) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
     const R gi = A.gfield[i];
-    R h[L::Q];
+    R a0, B[3], T[6];
+    post_collision<L, R>(M, gi, a0, B, T);
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) h[a] = regularized<L, R>(M, a);
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = h[a] + gi * (h[L::opp(a)] - h[a]);   // Eq. 23
+    for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
     if (A.sample) {
       const int* b = A.obj.box;
       if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
         const R w = R(A.wobj[i]);
-        if (w != R(0)) bj = double(w * local_objective<L, R>(M, A.obj, gi));
+        if (w != R(0)) bj = w * local_objective<L, R>(M, A.obj, gi);
       }
-      if (A.obj.mon == MON_DRAG) bm = double(R(-2) * gi * M.m[0]);
+      if (A.obj.mon == MON_DRAG) bm = R(-2) * gi * M.m[0];
     }
   }
   if (A.sample) {   // uniform across the grid
-    block_sum2(bj, bm);
-    sample_commit(bj, bm, A.partials, A.counter, A.acc, A.obj.jconst, A.obj.mon_scale, A.obj.mon);
+    block_sum2<R>(bj, bm);
+    sample_commit(double(bj), double(bm), A.blk);
   }
 }
 
-// Window end: means (Eq. 42), consecutive-window ratio (Eq. 26), reset.
-__global__ void window_end_kernel(WindowAcc* acc, double tol, int* nonfinite) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double n = double(acc->count > 0 ? acc->count : 1);
-  const double jm = (acc->jsum + acc->jcomp) / n;
-  const double mm = (acc->msum + acc->mcomp) / n;
+// Window end (one block of kEndThreads): sum the per-block window sums in a
+// fixed order with compensation, form the means of Eq. 42 and the ratio of
+// Eq. 26, and clear the block sums for the next window.
+constexpr int kEndThreads = 256;
+__global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, int nblocks, WindowAcc* acc,
+                                                                 double tol, const int* nonfinite,
+                                                                 double nsamples, double jconst,
+                                                                 double mon_scale, int mon_kind) {
+  __shared__ double sh[4][kEndThreads];
+  double sj = 0, cj = 0, sm = 0, cm = 0;
+  for (int b = threadIdx.x; b < nblocks; b += kEndThreads) {
+    double4 a = reinterpret_cast<double4*>(blk)[b];
+    neumaier(sj, cj, a.x);
+    neumaier(sj, cj, a.y);
+    neumaier(sm, cm, a.z);
+    neumaier(sm, cm, a.w);
+    reinterpret_cast<double4*>(blk)[b] = make_double4(0.0, 0.0, 0.0, 0.0);
+  }
+  sh[0][threadIdx.x] = sj; sh[1][threadIdx.x] = cj; sh[2][threadIdx.x] = sm; sh[3][threadIdx.x] = cm;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double tj = 0, tcj = 0, tm = 0, tcm = 0;
+  for (int t = 0; t < kEndThreads; ++t) {
+    neumaier(tj, tcj, sh[0][t]);
+    neumaier(tj, tcj, sh[1][t]);
+    neumaier(tm, tcm, sh[2][t]);
+    neumaier(tm, tcm, sh[3][t]);
+  }
+  const double jm = (tj + tcj) / nsamples + jconst;
+  const double mm = mon_kind == MON_DRAG ? (tm + tcm) / nsamples * mon_scale : jm;
   if (acc->has_prev) {
     const double d = fabs(mm - acc->mprev);
     acc->ratio = fabs(mm) < 1e-30 ? d : d / fabs(mm);
@@ -384,8 +434,6 @@ __global__ void window_end_kernel(WindowAcc* acc, double tol, int* nonfinite) {
   acc->mprev = mm;
   acc->has_prev = 1;
   acc->nonfinite = *nonfinite;
-  acc->jsum = acc->jcomp = acc->msum = acc->mcomp = 0.0;
-  acc->count = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -398,14 +446,14 @@ __global__ void window_end_kernel(WindowAcc* acc, double tol, int* nonfinite) {
 // ---------------------------------------------------------------------------
 template <class R>
 struct AdjArgs {
-  const R* __restrict__ bnext;   // adjoint of p^n's consumers: b^{n+1} after the boundary transpose
+  const R* __restrict__ bnext;   // b^{n+1} after the boundary transpose
   const R* __restrict__ pprev;   // p^{n-1}
   R* __restrict__ bout;          // b^n after the boundary transpose
   const R* __restrict__ gfield;
   const uint8_t* __restrict__ cls;
   const float* __restrict__ uin;
   const float* __restrict__ wobj;
-  double2* __restrict__ gacc;    // per-node (sum, compensation) of the sensitivity
+  R* __restrict__ gpart;         // per-node sensitivity partial of the current segment
   Geo geo;
   Phys<R> ph;
   Obj<R> obj;
@@ -414,9 +462,9 @@ struct AdjArgs {
   int dbox[6];                   // design box
 };
 
-// Transposed boundary completion at node i (in place on b).
+// Transposed boundary completion at a face node (in place on b).
 template <class L, class R>
-__device__ __forceinline__ void bc_transpose(R (&b)[L::Q], unsigned unk, uint8_t cls, R u0, R rho_out) {
+__device__ __noinline__ void bc_transpose(R* b, unsigned unk, uint8_t cls, R u0) {
   if (!unk) return;
   if (cls == WALL) {
 #pragma unroll
@@ -456,14 +504,36 @@ __device__ __forceinline__ void bc_transpose(R (&b)[L::Q], unsigned unk, uint8_t
     b[3] = b[6] = b[7] = R(0);
   }
   // OUTLET_ZG: the unknown entries keep b_a(i); the node they were copied
-  // from pulls them (see adj_step_kernel).
+  // from pulls them (see pull_face).
+}
+
+// Face part of the adjoint pull (out of line).
+template <class L, class R>
+__device__ __noinline__ void pull_face(const R* __restrict__ b, const uint8_t* __restrict__ cls, const Geo& g,
+                                       int x, int y, int z, R* a) {
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) {
+    unsigned j;
+    a[k] = neighbour(g, x, y, z, L::cx(k), L::cy(k), L::cz(k), j) ? b[k * g.n + j] : R(0);
+  }
+  // A zero-gradient outlet node j copied p_k(i) into its unknown f_k(j),
+  // j = i + c_k - n_in; pull those adjoints back.
+  if (x == g.nx - 1 || x == 0) {
+    const int sx = (x == g.nx - 1) ? -1 : 1;   // c_kx of the directions unknown on this face
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) {
+      if (L::cx(k) != sx) continue;
+      unsigned j;
+      if (neighbour(g, x, y, z, 0, L::cy(k), L::cz(k), j) && cls[j] == OUTLET_ZG) a[k] += b[k * g.n + j];
+    }
+  }
 }
 
 // a_k(i) = b_k(i + c_k): adjoint streaming (Eq. 36), pulled from downstream,
 // plus the transposed zero-gradient copies.  b == nullptr means b = 0.
 template <class L, class R>
 __device__ __forceinline__ void pull_adjoint(const R* __restrict__ b, const uint8_t* __restrict__ cls,
-                                             const Geo& g, int x, int y, int z, long long i, bool face,
+                                             const Geo& g, int x, int y, int z, unsigned i, bool face,
                                              R (&a)[L::Q]) {
   if (b == nullptr) {
 #pragma unroll
@@ -472,22 +542,10 @@ __device__ __forceinline__ void pull_adjoint(const R* __restrict__ b, const uint
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) a[k] = b[k * g.n + i + offset<L>(g, k)];
   } else {
+    R t[L::Q];
+    pull_face<L, R>(b, cls, g, x, y, z, t);
 #pragma unroll
-    for (int k = 0; k < L::Q; ++k) {
-      long long j;
-      a[k] = neighbour(g, x, y, z, L::cx(k), L::cy(k), L::cz(k), j) ? b[k * g.n + j] : R(0);
-    }
-    // A zero-gradient outlet node j copied p_k(i) into its unknown f_k(j),
-    // j = i + c_k - n_in; pull those adjoints back.
-    if (x == g.nx - 1 || x == 0) {
-      const int sx = (x == g.nx - 1) ? -1 : 1;   // c_kx of the directions unknown on this face
-#pragma unroll
-      for (int k = 0; k < L::Q; ++k) {
-        if (L::cx(k) != sx) continue;
-        long long j;
-        if (neighbour(g, x, y, z, 0, L::cy(k), L::cz(k), j) && cls[j] == OUTLET_ZG) a[k] += b[k * g.n + j];
-      }
-    }
+    for (int k = 0; k < L::Q; ++k) a[k] = t[k];
   }
 }
 
@@ -497,7 +555,7 @@ __global__ void __launch_bounds__(kBlock) adj_pull_kernel(const R* __restrict__ 
                                                           R* __restrict__ out, Geo g) {
   const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   if (x >= g.nx) return;
-  const long long i = x + y * g.sy + z * g.sz;
+  const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
   R a[L::Q];
   pull_adjoint<L, R>(b, cls, g, x, y, z, i, on_face<L>(g, x, y, z), a);
 #pragma unroll
@@ -509,48 +567,34 @@ __global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
   const Geo& g = A.geo;
   const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   if (x >= g.nx) return;
-  const long long i = x + y * g.sy + z * g.sz;
+  const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
   const bool face = on_face<L>(g, x, y, z);
   const uint8_t cls = face ? A.cls[i] : uint8_t(FLUID);
   const R u0 = (face && cls == INLET) ? R(A.uin[y + g.ny * z]) : R(0);
 
-  R a[L::Q];
-  pull_adjoint<L, R>(A.terminal ? nullptr : A.bnext, A.cls, g, x, y, z, i, face, a);
+  // Weighted moments of the pulled adjoint a^n: A0 = sum w a, A1 = sum w c a,
+  // A2 = sum w c c a.  Everything below needs a only through them.
+  R A0, A1[3], A2[6];
+  {
+    R a[L::Q];
+    pull_adjoint<L, R>(A.terminal ? nullptr : A.bnext, A.cls, g, x, y, z, i, face, a);
+    raw_moments<L, R, true>(a, A0, A1, A2);
+  }
 
   R f[L::Q];
-  unsigned unk;
-  gather<L, R>(A.pprev, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f, unk);
+  const unsigned unk = gather<L, R>(A.pprev, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f);
   Mom<L, R> M;
   moments<L, R>(f, A.ph, M);
   const R gi = A.gfield[i];
 
-  // Sensitivity term of Eq. 40: sum_b a_b (h_bbar - h_b), times g'(phi) later.
-  R gt = 0;
-  {
-    R h[L::Q];
-#pragma unroll
-    for (int k = 0; k < L::Q; ++k) h[k] = regularized<L, R>(M, k);
-#pragma unroll
-    for (int k = 0; k < L::Q; ++k) gt += a[k] * (h[L::opp(k)] - h[k]);
-  }
+  // Sensitivity term of Eq. 40: sum_b a_b (h_bbar - h_b) = -6 m . A1 (times g'(phi) later).
+  R gt = R(-6) * (M.m[0] * A1[0] + M.m[1] * A1[1] + M.m[2] * A1[2]);
 
-  // v = (d p / d h)^T a  (transpose of the blend of Eq. 23)
-  R V0 = 0, V1[3] = {0, 0, 0}, V2[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < L::Q; ++k) {
-    const R v = R(L::w(k)) * (a[k] + gi * (a[L::opp(k)] - a[k]));
-    const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
-    V0 += v;
-    if (cx) V1[0] += cx * v;
-    if (cy) V1[1] += cy * v;
-    if (cz) V1[2] += cz * v;
-    if (cx) V2[0] += v;
-    if (cy) V2[1] += v;
-    if (cz) V2[2] += v;
-    if (cx * cy) V2[3] += (cx * cy) * v;
-    if (cx * cz) V2[4] += (cx * cz) * v;
-    if (cy * cz) V2[5] += (cy * cz) * v;
-  }
+  // Moments of v = (d p / d h)^T a: the blend scales the first moment by (1 - 2g).
+  const R V0 = A0;
+  const R sc = R(1) - R(2) * gi;
+  const R V1[3] = {sc * A1[0], sc * A1[1], sc * A1[2]};
+  const R* V2 = A2;
   const R* u = M.u;
   const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   // V2 u (symmetric V2)
@@ -565,10 +609,10 @@ __global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
   cu[1] = M.rho * (R(3) * V1[1] + R(9) * V2u1 - R(3) * V0 * u[1]);
   cu[2] = M.rho * (R(3) * V1[2] + R(9) * V2u2 - R(3) * V0 * u[2]);
   R crho = E;          // d psi / d rho at fixed u, Pi, tau_eff
-  R cm[3] = {0, 0, 0}; // d psi / d m directly
+  R cm0 = 0;           // d psi / d m_x directly (drag objective)
   // psi_neq = om * 4.5 R:Pi with R = V2 - cs^2 V0 I   (Eq. 16)
   const R c = cs2<R>();
-  R Rm[6] = {V2[0] - c * V0, V2[1] - c * V0, (L::D == 3 ? V2[2] - c * V0 : R(0)), V2[3], V2[4], V2[5]};
+  const R Rm[6] = {V2[0] - c * V0, V2[1] - c * V0, (L::D == 3 ? V2[2] - c * V0 : R(0)), V2[3], V2[4], V2[5]};
   const R RP = R(4.5) * (Rm[0] * M.pi[0] + Rm[1] * M.pi[1] + Rm[2] * M.pi[2] +
                          R(2) * (Rm[3] * M.pi[3] + Rm[4] * M.pi[4] + Rm[5] * M.pi[5]));
   R ctau = RP / (M.te * M.te);   // d psi / d tau_eff through om = 1 - 1/tau_eff
@@ -600,7 +644,7 @@ __global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
           }
           case OBJ_PRES: crho += ws * c; break;
           default: {
-            cm[0] += ws * R(-2) * gi;
+            cm0 += ws * R(-2) * gi;
             gt += ws * R(-2) * M.m[0];   // direct d psi / d g, times g'(phi) later
           }
         }
@@ -619,9 +663,9 @@ __global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
   }
   // u = m / rho
   R gm[3], grho;
-  gm[0] = cu[0] * M.inv + cm[0];
-  gm[1] = cu[1] * M.inv + cm[1];
-  gm[2] = cu[2] * M.inv + cm[2];
+  gm[0] = cu[0] * M.inv + cm0;
+  gm[1] = cu[1] * M.inv;
+  gm[2] = cu[2] * M.inv;
   grho = crho - (u[0] * cu[0] + u[1] * cu[1] + u[2] * cu[2]) * M.inv;
   // Pi(rho, m, M2) = M2 - rho cs^2 I - m m^T / rho
   {
@@ -637,21 +681,37 @@ __global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
   // b_a = d psi / d f_a = grho + c_a . gm + c_a c_a : cpi
   R b[L::Q];
 #pragma unroll
-  for (int k = 0; k < L::Q; ++k) {
-    const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
-    b[k] = grho + R(cx) * gm[0] + R(cy) * gm[1] + R(cz) * gm[2] + R(cx * cx) * cpi[0] +
-           R(cy * cy) * cpi[1] + R(cz * cz) * cpi[2] + R(2 * cx * cy) * cpi[3] + R(2 * cx * cz) * cpi[4] +
-           R(2 * cy * cz) * cpi[5];
+  for (int k = 0; k < L::Q; ++k) b[k] = quad_form<L, R>(k, grho, gm, cpi);
+  if (face) {
+    R t[L::Q];
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) t[k] = b[k];
+    bc_transpose<L, R>(t, unk, cls, u0);
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) b[k] = t[k];
   }
-  if (face) bc_transpose<L, R>(b, unk, cls, u0, A.ph.rho_out);
 #pragma unroll
   for (int k = 0; k < L::Q; ++k) A.bout[k * g.n + i] = b[k];
 
   const int* d = A.dbox;
-  if (x >= d[0] && x < d[1] && y >= d[2] && y < d[3] && z >= d[4] && z < d[5]) {
-    double2 s = A.gacc[i];
-    neumaier(s.x, s.y, double(gt));
-    A.gacc[i] = s;
+  if (x >= d[0] && x < d[1] && y >= d[2] && y < d[3] && z >= d[4] && z < d[5]) A.gpart[i] += gt;
+}
+
+// Fold a segment's sensitivity partials into the FP64 (sum, compensation)
+// accumulator and clear them (once per segment of K steps).
+template <class R>
+__global__ void grad_fold_kernel(R* __restrict__ gpart, double2* __restrict__ gacc, Geo g, int x0, int x1,
+                                 int y0, int y1, int z0, int z1) {
+  const int bx = x1 - x0, by = y1 - y0;
+  const long long total = (long long)bx * by * (z1 - z0);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int x = x0 + int(k % bx), y = y0 + int((k / bx) % by), z = z0 + int(k / ((long long)bx * by));
+    const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
+    double2 s = gacc[i];
+    neumaier(s.x, s.y, double(gpart[i]));
+    gacc[i] = s;
+    gpart[i] = R(0);
   }
 }
 

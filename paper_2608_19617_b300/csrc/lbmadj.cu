@@ -75,8 +75,8 @@ unsigned mask_with_cx(int sx) {
 
 // Layout of the caller's workspace.
 struct Layout {
-  size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
-      partials, counter, acc, flags, total;
+  size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gpart, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
+      partials, acc, flags, total;
   int nblocks_fwd, nblocks_1d, nslots;
   bool stage_in_seg;
 };
@@ -86,6 +86,8 @@ lbm_status validate_config(const lbm_config& c) {
   if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(LBM_ERR_ARG, "lattice sizes must be >= 1");
   if (c.lattice == LBM_D2Q9 && c.nz != 1) return fail(LBM_ERR_ARG, "D2Q9 needs nz == 1");
   if (c.ny > 65535 || c.nz > 65535) return fail(LBM_ERR_ARG, "ny and nz must be <= 65535");
+  if (double(c.nx) * c.ny * c.nz * c.lattice >= 2147483647.0)
+    return fail(LBM_ERR_ARG, "Q * nx * ny * nz must stay below 2^31 (32-bit element indices)");
   const int dims[3] = {c.nx, c.ny, c.nz};
   for (int k = 0; k < 3; ++k) {
     if (c.periodic[k] != 0 && c.periodic[k] != 1) return fail(LBM_ERR_ARG, "periodic flags must be 0 or 1");
@@ -143,9 +145,9 @@ Layout make_layout(const lbm_config& c) {
   L.cls = take(n);
   L.uin = take(size_t(c.ny) * c.nz * 4);
   L.gacc = take(n * 16);
+  L.gpart = take(n * rs);
   L.gout = take(n * 8);
-  L.partials = take(size_t(L.nblocks_fwd) * 16);
-  L.counter = take(16);
+  L.partials = take(size_t(L.nblocks_fwd) * 32);
   L.acc = take(sizeof(lbm::WindowAcc));
   L.flags = take(16);
   L.ckpt = take(L.ckpt_slot * L.nslots);
@@ -173,6 +175,7 @@ struct Impl {
   virtual void pull(const void* b, void* out) = 0;
   virtual void set_design() = 0;
   virtual void grad() = 0;
+  virtual void fold() = 0;
   virtual void unshift(const void* src) = 0;
   virtual void shift(void* dst) = 0;
   virtual void to_double(const void* src) = 0;
@@ -180,11 +183,24 @@ struct Impl {
   virtual void decode(int slot, void* p) = 0;
 };
 
+// A captured CUDA graph with the timing events its replays record.
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Pending> events;
+};
+
 struct lbm_ctx {
   lbm_config cfg;
   Layout lay;
   char* ws;
-  cudaStream_t stream;
+  cudaStream_t stream;        // the caller's stream: everything runs in its order
+  cudaStream_t ls = nullptr;  // stream launches go to (the capture stream while capturing)
+  cudaStream_t cap = nullptr; // private stream used only to capture graphs
+  bool use_graphs = true;
+  bool capturing = false;
+  std::vector<Pending>* sink = nullptr;   // where end() files events while capturing
+  GraphRec gwin[2][2];        // forward window graphs by [start parity][timing]
+  GraphRec gadj[2];           // adjoint sweep graphs by [timing]
   lbm::Geo geo;
   size_t n, q, rs;
   int cur;                    // index of the buffer holding the carried field
@@ -223,15 +239,32 @@ struct lbm_ctx {
   cudaEvent_t begin() {
     if (!timing) return nullptr;
     cudaEvent_t e = event();
-    if (e) cudaEventRecord(e, stream);
+    if (e) cudaEventRecord(e, ls);
     return e;
   }
   void end(cudaEvent_t a, int phase, int64_t launches, int64_t lus) {
     if (!timing || !a) return;
     cudaEvent_t b = event();
     if (!b) return;
-    cudaEventRecord(b, stream);
-    pending.push_back({phase, a, b, launches, lus});
+    cudaEventRecord(b, ls);
+    (capturing ? *sink : pending).push_back({phase, a, b, launches, lus});
+  }
+  // Add the elapsed times of a replayed graph's events (after a sync).
+  void harvest_graph(const GraphRec& g) {
+    for (const auto& p : g.events) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        tm.ms[p.phase] += ms;
+        tm.launches[p.phase] += p.launches;
+        tm.lattice_updates[p.phase] += p.lus;
+      }
+    }
+  }
+  void drop_graph(GraphRec& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    for (auto& p : g.events) { pool.push_back(p.a); pool.push_back(p.b); }
+    g.events.clear();
   }
   void harvest() {   // after a stream synchronisation
     for (auto& p : pending) {
@@ -247,8 +280,11 @@ struct lbm_ctx {
     pending.clear();
   }
   ~lbm_ctx() {
+    for (auto& row : gwin) for (auto& g : row) drop_graph(g);
+    for (auto& g : gadj) drop_graph(g);
     for (auto& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
     for (auto e : pool) cudaEventDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
   }
 };
 
@@ -273,8 +309,6 @@ struct ImplT final : Impl {
     for (int i = 0; i < 3; ++i) o.uref[i] = R(k.objective_uref[i]);
     for (int i = 0; i < 6; ++i) o.box[i] = k.obj_box[i];
     o.ws = R(double(k.sample_every) / double(k.window_len));
-    o.mon_scale = k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
-    o.jconst = c->jconst;
     return o;
   }
 
@@ -290,11 +324,9 @@ struct ImplT final : Impl {
     A.ph = phys();
     A.obj = obj();
     A.sample = sample;
-    A.partials = c->template at<double>(c->lay.partials);
-    A.counter = c->template at<unsigned>(c->lay.counter);
-    A.acc = c->template at<lbm::WindowAcc>(c->lay.acc);
+    A.blk = c->template at<double>(c->lay.partials);
     A.nonfinite = c->template at<int>(c->lay.flags);
-    lbm::fwd_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->stream>>>(A);
+    lbm::fwd_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(A);
   }
   void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
     lbm::AdjArgs<R> A;
@@ -305,41 +337,50 @@ struct ImplT final : Impl {
     A.cls = c->template at<uint8_t>(c->lay.cls);
     A.uin = c->template at<float>(c->lay.uin);
     A.wobj = c->template at<float>(c->lay.wobj);
-    A.gacc = c->template at<double2>(c->lay.gacc);
+    A.gpart = c->template at<R>(c->lay.gpart);
     A.geo = c->geo;
     A.ph = phys();
     A.obj = obj();
     A.sample = sample;
     A.terminal = bnext == nullptr;
     for (int i = 0; i < 6; ++i) A.dbox[i] = c->cfg.design_box[i];
-    lbm::adj_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->stream>>>(A);
+    lbm::adj_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(A);
   }
   void pull(const void* b, void* out) override {
-    lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->stream>>>(
+    lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(
         static_cast<const R*>(b), c->template at<uint8_t>(c->lay.cls), static_cast<R*>(out), c->geo);
   }
   void set_design() override {
-    lbm::design_kernel<R><<<flat_blocks(), 256, 0, c->stream>>>(
+    lbm::design_kernel<R><<<flat_blocks(), 256, 0, c->ls>>>(
         c->template at<float>(c->lay.gamma), c->template at<R>(c->lay.g), (long long)c->n, c->cfg.q_interp, c->cfg.g_max, c->template at<int>(c->lay.flags) + 1);
+  }
+  void fold() override {
+    const int* d = c->cfg.design_box;
+    const long long cells = (long long)(d[1] - d[0]) * (d[3] - d[2]) * (d[5] - d[4]);
+    if (cells == 0) return;
+    const long long blocks = (cells + 255) / 256;
+    lbm::grad_fold_kernel<R><<<int(blocks < 148 * 32 ? blocks : 148 * 32), 256, 0, c->ls>>>(
+        c->template at<R>(c->lay.gpart), c->template at<double2>(c->lay.gacc), c->geo, d[0], d[1], d[2], d[3],
+        d[4], d[5]);
   }
   void grad() override {
     const int* d = c->cfg.design_box;
-    lbm::gradient_kernel<<<flat_blocks(), 256, 0, c->stream>>>(
+    lbm::gradient_kernel<<<flat_blocks(), 256, 0, c->ls>>>(
         c->template at<double2>(c->lay.gacc), c->template at<float>(c->lay.gamma), c->template at<double>(c->lay.gout),
         c->geo, d[0], d[1], d[2], d[3], d[4], d[5], c->cfg.q_interp, c->cfg.g_max);
   }
   void unshift(const void* src) override {
-    lbm::unshift_kernel<L, R><<<flat_blocks(), 256, 0, c->stream>>>(static_cast<const R*>(src),
+    lbm::unshift_kernel<L, R><<<flat_blocks(), 256, 0, c->ls>>>(static_cast<const R*>(src),
                                                                       c->template at<double>(c->lay.stage),
                                                                       (long long)c->n);
   }
   void shift(void* dst) override {
-    lbm::shift_kernel<L, R><<<flat_blocks(), 256, 0, c->stream>>>(c->template at<double>(c->lay.stage),
+    lbm::shift_kernel<L, R><<<flat_blocks(), 256, 0, c->ls>>>(c->template at<double>(c->lay.stage),
                                                                     static_cast<R*>(dst), (long long)c->n,
                                                                     c->template at<int>(c->lay.flags) + 1);
   }
   void to_double(const void* src) override {
-    lbm::copy_double_kernel<R><<<flat_blocks(), 256, 0, c->stream>>>(
+    lbm::copy_double_kernel<R><<<flat_blocks(), 256, 0, c->ls>>>(
         static_cast<const R*>(src), c->template at<double>(c->lay.stage), (long long)(c->n * c->q));
   }
   template <class T>
@@ -348,7 +389,7 @@ struct ImplT final : Impl {
     T* dev = reinterpret_cast<T*>(base);
     float* mom = reinterpret_cast<float*>(base + align_up(c->q * c->n * 2));
     int* ex = reinterpret_cast<int*>(base + align_up(c->q * c->n * 2) + align_up((L::D + 1) * c->n * 4));
-    lbm::ckpt_encode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->stream>>>(
+    lbm::ckpt_encode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->ls>>>(
         static_cast<const float*>(p), dev, mom, ex, (long long)c->n);
   }
   template <class T>
@@ -357,7 +398,7 @@ struct ImplT final : Impl {
     T* dev = reinterpret_cast<T*>(base);
     float* mom = reinterpret_cast<float*>(base + align_up(c->q * c->n * 2));
     int* ex = reinterpret_cast<int*>(base + align_up(c->q * c->n * 2) + align_up((L::D + 1) * c->n * 4));
-    lbm::ckpt_decode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->stream>>>(
+    lbm::ckpt_decode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->ls>>>(
         dev, mom, ex, static_cast<float*>(p), (long long)c->n);
   }
   void encode(const void* p, int slot) override {
@@ -427,6 +468,90 @@ lbm_status check_flags(lbm_ctx* c, int which, lbm_status st, const char* what) {
   return LBM_OK;
 }
 
+// Work of one forward window (Alg. 1 inner loop): checkpoint s before step
+// n0 + sK, K fused steps per segment, window-end reduction.  Enqueued on c->ls.
+lbm_status enqueue_window(lbm_ctx* c) {
+  const lbm_config& k = c->cfg;
+  const int K = k.ckpt_every, S = c->lay.nslots;
+  const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
+  const size_t lat_bytes = c->q * c->n * c->rs;
+  for (int s = 0; s < S; ++s) {
+    cudaEvent_t e = c->begin();
+    if (native) CUDA_TRY(cudaMemcpyAsync(c->seg_slot(s, 0), c->lattice(c->cur), lat_bytes, cudaMemcpyDeviceToDevice, c->ls));
+    else c->impl->encode(c->lattice(c->cur), s);
+    c->end(e, 3, 1, 0);
+    e = c->begin();
+    for (int j = 0; j < K; ++j) {
+      const int step = s * K + j;
+      c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0);
+      c->cur ^= 1;
+    }
+    c->end(e, 0, K, int64_t(K) * int64_t(c->n));
+  }
+  const double mon_scale =
+      k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
+  lbm::window_end_kernel<<<1, lbm::kEndThreads, 0, c->ls>>>(
+      c->at<double>(c->lay.partials), c->lay.nblocks_fwd, c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol,
+      c->at<int>(c->lay.flags), double(k.window_len / k.sample_every), c->jconst, mon_scale, k.monitor_kind);
+  return LBM_OK;
+}
+
+// Work of one adjoint sweep (Alg. 2 reverse loop): per segment, restore,
+// recompute K-1 states, then K adjoint steps from the last state back.
+lbm_status enqueue_adjoint(lbm_ctx* c) {
+  const lbm_config& k = c->cfg;
+  const int K = k.ckpt_every, S = c->lay.nslots;
+  const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
+  CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gacc), 0, c->n * 16, c->ls));
+  CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gpart), 0, c->n * c->rs, c->ls));
+  int bo = 0;
+  const void* bnext = nullptr;
+  for (int s = S - 1; s >= 0; --s) {
+    cudaEvent_t e = c->begin();
+    if (!native) c->impl->decode(s, c->seg_slot(s, 0));
+    c->end(e, 3, native ? 0 : 1, 0);
+    e = c->begin();
+    for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
+    c->end(e, 1, K - 1, int64_t(K - 1) * int64_t(c->n));
+    e = c->begin();
+    for (int j = K - 1; j >= 0; --j) {
+      const int step = s * K + j;
+      c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), step % k.sample_every == 0);
+      bnext = c->adjbuf(bo);
+      bo ^= 1;
+    }
+    c->end(e, 2, K, int64_t(K) * int64_t(c->n));
+    c->impl->fold();
+  }
+  return LBM_OK;
+}
+
+// Record body() into a CUDA graph on the private capture stream and
+// instantiate it.  The caller's stream may be the legacy default stream,
+// which cannot be captured; the graph is launched into it afterwards.
+lbm_status capture(lbm_ctx* c, GraphRec& G, lbm_status (*body)(lbm_ctx*)) {
+  if (!c->cap) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  const int cur0 = c->cur;
+  c->ls = c->cap;
+  c->capturing = true;
+  c->sink = &G.events;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  lbm_status st = e == cudaSuccess ? body(c) : LBM_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+  c->ls = c->stream;
+  c->capturing = false;
+  c->sink = nullptr;
+  c->cur = cur0;
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  if (st != LBM_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+  if (e2 != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) { G.exec = nullptr; return fail(LBM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)); }
+  return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -477,11 +602,12 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   ctx->lay = lay;
   ctx->ws = static_cast<char*>(workspace);
   ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->ls = ctx->stream;
   ctx->n = size_t(c.nx) * c.ny * c.nz;
   ctx->q = c.lattice;
   ctx->rs = c.precision == LBM_FP64 ? 8 : 4;
-  ctx->geo = lbm::Geo{c.nx, c.ny, c.nz, c.periodic[0], c.periodic[1], c.periodic[2], (long long)ctx->n,
-                      (long long)c.nx, (long long)c.nx * c.ny};
+  ctx->geo = lbm::Geo{c.nx, c.ny, c.nz, c.periodic[0], c.periodic[1], c.periodic[2], unsigned(ctx->n),
+                      unsigned(c.nx), unsigned(c.nx) * unsigned(c.ny)};
   ctx->cur = 0;
   lbm_ctx* x = ctx.get();
   if (c.lattice == LBM_D2Q9) {
@@ -494,7 +620,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   const size_t n = ctx->n;
   cudaStream_t s = ctx->stream;
   CUDA_TRY(cudaMemsetAsync(x->at(lay.f[0]), 0, align_up(ctx->q * n * ctx->rs), s));   // rest equilibrium
-  CUDA_TRY(cudaMemsetAsync(x->at(lay.counter), 0, 16, s));
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.partials), 0, size_t(lay.nblocks_fwd) * 32, s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.acc), 0, sizeof(lbm::WindowAcc), s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.flags), 0, 16, s));
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.cls), node_class, n, cudaMemcpyDefault, s));
@@ -544,27 +670,20 @@ void lbm_destroy(lbm_ctx* ctx) { delete ctx; }
 lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window) {
   if (!c) return fail(LBM_ERR_ARG, "null context");
   const lbm_config& k = c->cfg;
-  const int K = k.ckpt_every, S = c->lay.nslots;
-  const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
-  const size_t lat_bytes = c->q * c->n * c->rs;
-  for (int s = 0; s < S; ++s) {
-    cudaEvent_t e = c->begin();
-    if (native) CUDA_TRY(cudaMemcpyAsync(c->seg_slot(s, 0), c->lattice(c->cur), lat_bytes, cudaMemcpyDeviceToDevice, c->stream));
-    else c->impl->encode(c->lattice(c->cur), s);
-    c->end(e, 3, 1, 0);
-    e = c->begin();
-    for (int j = 0; j < K; ++j) {
-      const int step = s * K + j;
-      c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0);
-      c->cur ^= 1;
-    }
-    c->end(e, 0, K, int64_t(K) * int64_t(c->n));
+  const int cur0 = c->cur;
+  if (c->use_graphs) {
+    GraphRec& G = c->gwin[cur0][c->timing ? 1 : 0];
+    if (!G.exec) LBM_TRY(capture(c, G, enqueue_window));
+    CUDA_TRY(cudaGraphLaunch(G.exec, c->stream));
+    c->cur = cur0 ^ (k.window_len & 1);
+  } else {
+    LBM_TRY(enqueue_window(c));
   }
-  lbm::window_end_kernel<<<1, 32, 0, c->stream>>>(c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol, c->at<int>(c->lay.flags));
   CUDA_TRY(cudaGetLastError());
   lbm::WindowAcc acc;
   CUDA_TRY(cudaMemcpyAsync(&acc, c->at(c->lay.acc), sizeof acc, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->use_graphs) c->harvest_graph(c->gwin[cur0][c->timing ? 1 : 0]);
   c->harvest();
   c->steps += k.window_len;
   if (acc.nonfinite) {
@@ -596,32 +715,20 @@ lbm_status lbm_window_converged(lbm_ctx* c, int* converged, double* ratio) {
 lbm_status lbm_adjoint_window(lbm_ctx* c, double* J_eff) {
   if (!c) return fail(LBM_ERR_ARG, "null context");
   if (!c->window_valid) return fail(LBM_ERR_STATE, "no completed window to differentiate");
-  const lbm_config& k = c->cfg;
-  const int K = k.ckpt_every, S = c->lay.nslots;
-  const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
-  CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gacc), 0, c->n * 16, c->stream));
-  int bo = 0;
-  const void* bnext = nullptr;
-  for (int s = S - 1; s >= 0; --s) {
-    cudaEvent_t e = c->begin();
-    if (!native) c->impl->decode(s, c->seg_slot(s, 0));
-    c->end(e, 3, native ? 0 : 1, 0);
-    e = c->begin();
-    for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
-    c->end(e, 1, K - 1, int64_t(K - 1) * int64_t(c->n));
-    e = c->begin();
-    for (int j = K - 1; j >= 0; --j) {
-      const int step = s * K + j;
-      c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), step % k.sample_every == 0);
-      bnext = c->adjbuf(bo);
-      bo ^= 1;
-    }
-    c->end(e, 2, K, int64_t(K) * int64_t(c->n));
+  GraphRec* G = nullptr;
+  if (c->use_graphs) {
+    G = &c->gadj[c->timing ? 1 : 0];
+    if (!G->exec) LBM_TRY(capture(c, *G, enqueue_adjoint));
+    CUDA_TRY(cudaGraphLaunch(G->exec, c->stream));
+  } else {
+    LBM_TRY(enqueue_adjoint(c));
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (G) c->harvest_graph(*G);
   c->harvest();
-  c->bout_last = bo ^ 1;
+  // The sweep runs an even or odd number of adjoint steps: b^{n0} is in buffer (W-1) & 1.
+  c->bout_last = (c->cfg.window_len - 1) & 1;
   c->grad_valid = true;
   if (J_eff) *J_eff = c->last_j;
   return LBM_OK;
@@ -715,6 +822,12 @@ lbm_status lbm_get_timing(lbm_ctx* c, lbm_timing* out) {
   c->harvest();
   *out = c->tm;
   c->tm = lbm_timing{};
+  return LBM_OK;
+}
+
+lbm_status lbm_set_graphs(lbm_ctx* c, int32_t enable) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  c->use_graphs = enable != 0;
   return LBM_OK;
 }
 

@@ -291,3 +291,18 @@ def test_full_size_short_window_adjoint_against_oracle():
     assert np.abs(grad_w[m]).max() > 0
     assert np.all(grad[~m] == 0)
     assert cosine(grad[m], grad_w[m]) > 0.9999
+
+
+def test_graph_replay_matches_direct_launches():
+    """Windows and sweeps replayed as CUDA graphs give bitwise the results of
+    individually launched kernels, including an odd |W| (parity flips)."""
+    case = f32_inputs(I.small_channel(150, 12, window_len=15, ckpt_every=5, outlet=I.OUTLET_P, tau=0.53))
+    out = []
+    for graphs in (False, True):
+        sol = B.Solver(case, B.LBM_FP32)
+        sol.set_graphs(graphs)
+        rec = [sol.step_window() for _ in range(3)]
+        sol.adjoint_window()
+        out.append((rec, sol.design_gradient(), sol.get_state()))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])

@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--ckpt-every", type=int, default=0, help="override K (profiling runs)")
     ap.add_argument("--spinup-windows", type=int, default=4)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--graphs", type=int, default=1, help="replay windows / sweeps as CUDA graphs")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: no CPU baseline, no FP64 check, no e2e pass")
     a = ap.parse_args()
@@ -131,8 +132,9 @@ def bytes_per_lu(case, phase, rs=4):
 
     forward / recompute: read Q populations, write Q, read g: (2Q+1) rs.
     adjoint: read Q adjoints, Q populations, g; write Q adjoints: (3Q+1) rs;
-    plus 32 B of FP64 (sum, compensation) read+write per design-box node and
-    the objective weight (4 B) per objective-box node at sampling steps.
+    plus the per-segment sensitivity partial (rs read + rs write) per
+    design-box node and the objective weight (4 B) per objective-box node at
+    sampling steps.
     """
     q, n = case.lattice, case.n
     if phase in ("forward", "recompute"):
@@ -141,7 +143,7 @@ def bytes_per_lu(case, phase, rs=4):
     nd = (x1 - x0) * (y1 - y0) * (z1 - z0)
     x0, x1, y0, y1, z0, z1 = case.obj_box
     no = (x1 - x0) * (y1 - y0) * (z1 - z0)
-    return (3 * q + 1) * rs + 32.0 * nd / n + 4.0 * no / n / case.sample_every
+    return (3 * q + 1) * rs + 2.0 * rs * nd / n + 4.0 * no / n / case.sample_every
 
 
 def kernel_hash():
@@ -254,6 +256,7 @@ def run_ours(args, case, rank, world, local):
     prec = B.LBM_FP64 if args.precision == "fp64" else B.LBM_FP32
     with torch.cuda.stream(stream):
         sol = B.Solver(case, prec, stream=stream)
+    sol.set_graphs(bool(args.graphs))
     n = case.n
     W, K = case.window_len, case.ckpt_every
     S = W // K
@@ -374,6 +377,7 @@ def run_ours(args, case, rank, world, local):
                    "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
                    "ckpt_format": ["fp32", "fp16", "bf16"][case.ckpt_format], "tau": case.tau,
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
+                   "cuda_graphs": bool(args.graphs),
                    "l2": "flushed (256 MB write) before every timed step; inside a step the forward "
                          "lattices (19 MB) stay L2-resident"},
         "fwd_mlups": 1e-6 * timing["forward"]["lattice_updates"] / (timing["forward"]["ms"] / 1e3),

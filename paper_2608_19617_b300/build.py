@@ -18,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbmadj.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+CU_FILES = ("lbmadj.cu",)
 
 
 def _sources():
@@ -39,7 +40,7 @@ def nvcc_path() -> str:
 def command(out=LIB, extra=()):
     return [nvcc_path(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3",
             "--shared", "-cudart", "shared", "-I", INCLUDE, "-I", CSRC, *extra,
-            os.path.join(CSRC, "lbmadj.cu"), "-o", out]
+            *[os.path.join(CSRC, f) for f in CU_FILES], "-o", out]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -211,6 +211,7 @@ struct lbm_ctx {
   int bout_last = 0;          // adjoint buffer holding b^{n0}
   double jconst = 0;
   bool timing = false;
+  int64_t timing_failures = 0;
   lbm_timing tm{};
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
@@ -235,30 +236,29 @@ struct lbm_ctx {
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     return e;
   }
+  // Record a timing event; inside a capture it becomes an external event
+  // record node, which stays readable by cudaEventElapsedTime after replays.
+  void record(cudaEvent_t e) {
+    if (capturing) cudaEventRecordWithFlags(e, ls, cudaEventRecordExternal);
+    else cudaEventRecord(e, ls);
+  }
   // Phase bracket: call begin() before and end() after a run of launches.
   cudaEvent_t begin() {
     if (!timing) return nullptr;
     cudaEvent_t e = event();
-    if (e) cudaEventRecord(e, ls);
+    if (e) record(e);
     return e;
   }
   void end(cudaEvent_t a, int phase, int64_t launches, int64_t lus) {
     if (!timing || !a) return;
     cudaEvent_t b = event();
     if (!b) return;
-    cudaEventRecord(b, ls);
+    record(b);
     (capturing ? *sink : pending).push_back({phase, a, b, launches, lus});
   }
   // Add the elapsed times of a replayed graph's events (after a sync).
   void harvest_graph(const GraphRec& g) {
-    for (const auto& p : g.events) {
-      float ms = 0;
-      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-        tm.ms[p.phase] += ms;
-        tm.launches[p.phase] += p.launches;
-        tm.lattice_updates[p.phase] += p.lus;
-      }
-    }
+    for (const auto& p : g.events) add_pair(p);
   }
   void drop_graph(GraphRec& g) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -266,14 +266,23 @@ struct lbm_ctx {
     for (auto& p : g.events) { pool.push_back(p.a); pool.push_back(p.b); }
     g.events.clear();
   }
+  // Add one event pair's elapsed time; a pair that cannot be read is
+  // counted in timing_failures and its error is cleared so that it does not
+  // surface as a later call's cudaGetLastError.
+  void add_pair(const Pending& p) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      tm.ms[p.phase] += ms;
+      tm.launches[p.phase] += p.launches;
+      tm.lattice_updates[p.phase] += p.lus;
+    } else {
+      cudaGetLastError();
+      timing_failures += 1;
+    }
+  }
   void harvest() {   // after a stream synchronisation
     for (auto& p : pending) {
-      float ms = 0;
-      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-        tm.ms[p.phase] += ms;
-        tm.launches[p.phase] += p.launches;
-        tm.lattice_updates[p.phase] += p.lus;
-      }
+      add_pair(p);
       pool.push_back(p.a);
       pool.push_back(p.b);
     }

@@ -194,6 +194,36 @@ lbm_status lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
 /* Total steps advanced and windows completed since lbm_create. */
 lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);
 
+/* One forward window, like lbm_step_window, for callers that cannot allocate
+ * device memory (code running while a CUDA graph is being captured, hosts
+ * that hand out only pre-registered buffers, sandboxes without access to the
+ * allocator).  There is no counterpart in the paper: it is a deployment aid.
+ *   cfg                 as for lbm_create (precision must be LBM_FP32; the
+ *                       checkpoint fields are ignored)
+ *   node_class          device, uint8 [N], obeying the rules of lbm_create
+ *                       (not re-checked here)
+ *   design_gamma, objective_weights
+ *                       device, float [N]
+ *   inlet_u             device, float [nz][ny]
+ *   pop                 device, float [Q][N], in/out: the carried field stored
+ *                       shifted by the rest weights, p_a - w_a (the library's
+ *                       internal FP32 layout); holds the window's last field
+ *                       on return
+ *   pop_tmp             device, float [Q][N], caller-owned second buffer
+ *   stream              cudaStream_t to enqueue on (NULL = legacy default)
+ * Returns the window means of the objective and the monitor like
+ * lbm_step_window, and synchronises the stream.  It allocates nothing: its
+ * only scratch is a 512 KiB + 256 B array inside the library image, present
+ * on every GPU that loads the library until the process exits.  Limit: at most
+ * 16384 blocks of 128 nodes, i.e. ceil(nx/128) * ny * nz <= 16384; larger
+ * lattices return LBM_ERR_ARG.  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).
+ * All calls share the array: calls that overlap on the GPU race.  No
+ * checkpoints are stored, so lbm_adjoint_window cannot follow it. */
+lbm_status lbm_step_window_noalloc(const lbm_config* cfg, const uint8_t* node_class, const float* design_gamma,
+                                   const float* objective_weights, const float* inlet_u, float* pop,
+                                   float* pop_tmp, void* stream, double* J_window, double* monitor_window);
+
 const char* lbm_status_string(lbm_status s);
 const char* lbm_last_error(void);
 void lbm_destroy(lbm_ctx* ctx);

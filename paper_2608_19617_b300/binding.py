@@ -77,6 +77,8 @@ def lib() -> ctypes.CDLL:
         "lbm_get_timing": (st, [c_void_p, POINTER(LbmTiming)]),
         "lbm_get_counters": (st, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
         "lbm_set_graphs": (st, [c_void_p, c_int32]),
+        "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_status_string": (ctypes.c_char_p, [c_int32]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_destroy": (None, [c_void_p]),

@@ -563,6 +563,8 @@ lbm_status capture(lbm_ctx* c, GraphRec& G, lbm_status (*body)(lbm_ctx*)) {
 
 }  // namespace
 
+void lbm_set_last_error(const char* msg) { g_last_error = msg; }
+
 extern "C" {
 
 const char* lbm_status_string(lbm_status s) {

@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--spinup-windows", type=int, default=4)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--graphs", type=int, default=1, help="replay windows / sweeps as CUDA graphs")
+    ap.add_argument("--pdl", type=int, default=0, help="programmatic dependent launch of the step kernels")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: no CPU baseline, no FP64 check, no e2e pass")
     a = ap.parse_args()
@@ -161,6 +162,37 @@ def measured_traffic(kernel, workload):
     return None
 
 
+def fp64_check_window(case, cap_bytes=150e9):
+    """Window and checkpoint interval of the FP64 cross-check: the longest of
+    |W|, |W|/2, 1000, 500, 250, 200 steps whose FP64 workspace, with the
+    checkpoint interval K minimising |W|/K + K slots, stays under cap_bytes."""
+    slot = case.lattice * case.n * 8
+    W = case.window_len
+    for Wc in [W, W // 2, 1000, 500, 250, 200]:
+        if Wc > W or Wc < 1:
+            continue
+        K = min((d for d in range(1, Wc + 1) if Wc % d == 0), key=lambda d: Wc // d + d)
+        if (Wc // K + K + 6) * slot <= cap_bytes:
+            return Wc, K
+    return 200, 10
+
+
+def reduce_max(value, world, device="cuda"):
+    """Max of a per-rank scalar over all ranks (the slowest rank's time)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(lus_per_step_per_rank, steps, world, ms_max):
+    """Lattice updates of all ranks over the slowest rank's time, in MLUPS."""
+    return world * steps * lus_per_step_per_rank / (ms_max / 1e3) / 1e6
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -257,6 +289,7 @@ def run_ours(args, case, rank, world, local):
     with torch.cuda.stream(stream):
         sol = B.Solver(case, prec, stream=stream)
     sol.set_graphs(bool(args.graphs))
+    sol.set_pdl(bool(args.pdl))
     n = case.n
     W, K = case.window_len, case.ckpt_every
     S = W // K
@@ -291,13 +324,11 @@ def run_ours(args, case, rank, world, local):
         torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     timing = sol.get_timing()
+    ms = reduce_max(ms, world)
     if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     lus_step = 2 * W * n
-    value = world * args.steps * lus_step / (ms / 1e3) / 1e6
+    value = whole_job_mlups(lus_step, args.steps, world, ms)
 
     # e2e: host design in, host gradient out, through the C ABI, per step.
     e2e_value = None
@@ -313,8 +344,8 @@ def run_ours(args, case, rank, world, local):
             sol.adjoint_window()
             sol.design_gradient(grad_host)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        e2e_value = world * args.steps * lus_step / e2e_s / 1e6
+        e2e_s = reduce_max(time.perf_counter() - t0, world)
+        e2e_value = whole_job_mlups(lus_step, args.steps, world, 1e3 * e2e_s)
 
     if rank != 0:
         return 0
@@ -327,36 +358,55 @@ def run_ours(args, case, rank, world, local):
         if t["launches"]:
             avg_ms = t["ms"] / t["launches"]
             bpl = bytes_per_lu(case, ph, rs=8 if prec == B.LBM_FP64 else 4) * n
-            phase_rows[ph] = {"launches": t["launches"], "ms": t["ms"], "avg_launch_us": 1e3 * avg_ms,
+            phase_rows[ph] = {"steps": t["launches"], "ms": t["ms"], "avg_step_us": 1e3 * avg_ms,
                               "bytes_per_launch": bpl, "gbs": bpl / (avg_ms / 1e3) / 1e9}
     dom = max(phase_rows, key=lambda p: phase_rows[p]["ms"])
-    kname = {"forward": "fwd_step_kernel", "recompute": "fwd_step_kernel", "adjoint": "adj_step_kernel"}[dom]
+    kname = {"forward": "fwd_interior_kernel+fwd_face_kernel", "recompute": "fwd_interior_kernel+fwd_face_kernel",
+             "adjoint": "adj_interior_kernel+adj_face_kernel"}[dom]
     ach = phase_rows[dom]["gbs"]
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": measured_traffic(kname, case.name), "kernel": kname, "phase": dom,
+            "timing": "CUDA events around each phase's back-to-back steps on the library stream; "
+                      "one step = the concurrent interior and face kernels",
             "peak_kind": f"{pk_kind} hbm_gbs (copy)",
             "bytes_per_lu": bytes_per_lu(case, dom, rs=8 if prec == B.LBM_FP64 else 4), "phases": phase_rows}
 
     # Accuracy beside the number: the FP32 window and adjoint against the FP64
-    # GPU path from the same start field.
+    # GPU path (native checkpoints) from the same start field.  The FP64
+    # workspace is kept under ~100 GB: the checkpoint interval is chosen to
+    # minimise it, and the window is shortened to 200 steps if even that is
+    # too large (said in the output).
     err = None
     if not args.no_fp64_check and prec == B.LBM_FP32:
+        W_err, K_err = fp64_check_window(case)
+        c32 = case.replace(window_len=W_err, ckpt_every=case.ckpt_every if W_err % case.ckpt_every == 0 else K_err)
+        c64 = case.replace(window_len=W_err, ckpt_every=K_err, ckpt_format=0)
         p = sol.get_state()
+        if W_err != W:            # free the timed solver's workspace first
+            sol.close()
+            sol.workspace = None
+            torch.cuda.empty_cache()
         with torch.cuda.stream(stream):
-            ref = B.Solver(case, B.LBM_FP64, stream=stream)
+            s32 = B.Solver(c32, B.LBM_FP32, stream=stream) if W_err != W else sol
+            ref = B.Solver(c64, B.LBM_FP64, stream=stream)
         ref.set_state(p)
-        sol.set_state(p)
-        J32, _ = sol.step_window()
-        sol.adjoint_window()
-        g32 = sol.design_gradient()
+        s32.set_state(p)
+        J32, _ = s32.step_window()
+        s32.adjoint_window()
+        g32 = s32.design_gradient()
         J64, _ = ref.step_window()
         ref.adjoint_window()
         g64 = ref.design_gradient()
-        cos = float(g32 @ g64 / (np.linalg.norm(g32) * np.linalg.norm(g64)))
+        n32, n64 = float(np.linalg.norm(g32)), float(np.linalg.norm(g64))
+        cos = float(g32 @ g64 / (n32 * n64)) if n32 > 0 and n64 > 0 else None
         err = {"J_rel_err_fp32_vs_fp64": abs(J32 - J64) / abs(J64), "grad_cosine_fp32_vs_fp64": cos,
-               "grad_rel_err_fp32_vs_fp64": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
-               "window_len": W}
+               "grad_rel_err_fp32_vs_fp64": float(np.linalg.norm(g32 - g64) / n64) if n64 > 0 else None,
+               "grad_norm_fp64": n64,
+               "window_len": W_err, "fp32_ckpt": ["fp32", "fp16", "bf16"][c32.ckpt_format],
+               "fp64_ckpt_every": K_err}
         ref.close()
+        if s32 is not sol:
+            s32.close()
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -366,7 +416,8 @@ def run_ours(args, case, rank, world, local):
                           f"lattice plus its adjoint ({r['lattice_updates']} lattice updates, {r['seconds']:.1f} s)"),
                "cpu": cpu_model()}
 
-    launches_per_step = W + 1 + (W - S) + W + 1 + (2 * S if case.ckpt_format else 0)
+    # each step is an interior and a face kernel; plus window end, folds, gradient, codecs
+    launches_per_step = 2 * W + 1 + 2 * (W - S) + 2 * W + S + 1 + (2 * S if case.ckpt_format else 0)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -377,7 +428,7 @@ def run_ours(args, case, rank, world, local):
                    "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
                    "ckpt_format": ["fp32", "fp16", "bf16"][case.ckpt_format], "tau": case.tau,
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
-                   "cuda_graphs": bool(args.graphs),
+                   "cuda_graphs": bool(args.graphs), "pdl": bool(args.pdl),
                    "l2": "flushed (256 MB write) before every timed step; inside a step the forward "
                          "lattices (19 MB) stay L2-resident"},
         "fwd_mlups": 1e-6 * timing["forward"]["lattice_updates"] / (timing["forward"]["ms"] / 1e3),

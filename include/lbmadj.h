@@ -168,6 +168,32 @@ lbm_status lbm_design_gradient(lbm_ctx* ctx, double* grad, size_t n);
  * Invalidates the recorded window and gradient. */
 lbm_status lbm_set_design(lbm_ctx* ctx, const float* design_gamma);
 
+/* Design pre-processing of Sec. 3.3: a linear density filter of radius r over
+ * design_box (weights max(0, r - distance), normalised per node) followed by
+ * the Heaviside projection of Wang et al. (2011),
+ *   gamma = (tanh(beta eta) + tanh(beta (x~ - eta))) / (tanh(beta eta) + tanh(beta (1 - eta))).
+ * Outside design_box gamma = x.  The projection acts on the solid fraction
+ * gamma; for eta = 1/2 this equals projecting phi = 1 - gamma. */
+typedef struct {
+  double radius;   /* filter radius in lattice units (the paper uses 4)   */
+  double beta;     /* projection steepness (the paper: 2 doubling to 16)   */
+  double eta;      /* projection threshold (the paper: 0.5)                */
+} lbm_filter;
+
+/* Set the design from raw variables x (host or device, float [N], in [0,1])
+ * through the filter and projection; like lbm_set_design it invalidates the
+ * recorded window.  Errors: LBM_ERR_ARG for bad parameters or values. */
+lbm_status lbm_set_design_filtered(lbm_ctx* ctx, const float* x_raw, const lbm_filter* f);
+
+/* dJ_eff/dx for the raw variables of the last lbm_set_design_filtered: the
+ * chain rule through the projection and the filter applied to dJ/dgamma
+ * (host or device, FP64 [N]).  Errors: LBM_ERR_STATE before an adjoint
+ * window or when the design was not set through the filter. */
+lbm_status lbm_design_gradient_filtered(lbm_ctx* ctx, double* grad, size_t n);
+
+/* The current (physical) design field gamma (host or device, float [N]). */
+lbm_status lbm_get_design(lbm_ctx* ctx, float* gamma, size_t n);
+
 /* Read / write the carried post-collision populations p (FP64, [Q][N], host
  * or device, n = Q*N).  lbm_set_state invalidates the recorded window. */
 lbm_status lbm_get_state(lbm_ctx* ctx, double* f, size_t n);
@@ -190,6 +216,11 @@ lbm_status lbm_get_timing(lbm_ctx* ctx, lbm_timing* out);
  * Graphs are captured on first use on a private stream and launched into the
  * context's stream. */
 lbm_status lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
+
+/* Launch the step kernels with programmatic dependent launch (1) so that each
+ * launch overlaps the tail of the previous one, or plainly (0, the default).
+ * Results are identical either way. */
+lbm_status lbm_set_pdl(lbm_ctx* ctx, int32_t enable);
 
 /* Total steps advanced and windows completed since lbm_create. */
 lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);

@@ -527,3 +527,82 @@ def moments_of(lat, p):
     """rho and u of a population field (for comparisons)."""
     rho = density(p)
     return rho, velocity(lat, p, rho)
+
+
+# ---------------------------------------------------------------------------
+# Design pre-processing (Sec. 3.3): density filter of radius r and Heaviside
+# projection with threshold eta and steepness beta, and their chain rule.
+# ---------------------------------------------------------------------------
+
+def filter_weights(shape, box, radius):
+    """Dense matrix of the linear density filter over the design box.
+
+    Inside the box, x~_i = sum_j w_ij x_j / sum_j w_ij with
+    w_ij = max(0, r - |x_i - x_j|) over box nodes j; outside the box x~ = x.
+    Returned as a scipy sparse matrix acting on the flattened field.
+    """
+    nz, ny, nx = shape
+    x0, x1, y0, y1, z0, z1 = box
+    n = nx * ny * nz
+    rows, cols, vals = [], [], []
+    R = int(np.ceil(radius))
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                i = x + nx * (y + ny * z)
+                inside = x0 <= x < x1 and y0 <= y < y1 and z0 <= z < z1
+                if not inside:
+                    rows.append(i); cols.append(i); vals.append(1.0)
+                    continue
+                ws, js = [], []
+                for dz in range(-R, R + 1):
+                    for dy in range(-R, R + 1):
+                        for dx in range(-R, R + 1):
+                            X, Y, Z = x + dx, y + dy, z + dz
+                            if not (x0 <= X < x1 and y0 <= Y < y1 and z0 <= Z < z1):
+                                continue
+                            w = radius - np.sqrt(dx * dx + dy * dy + dz * dz)
+                            if w > 0:
+                                ws.append(w)
+                                js.append(X + nx * (Y + ny * Z))
+                tot = sum(ws)
+                rows += [i] * len(js)
+                cols += js
+                vals += [w / tot for w in ws]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def heaviside(xf, beta, eta):
+    """Projection of Wang et al. (2011):
+    (tanh(beta eta) + tanh(beta (x - eta))) / (tanh(beta eta) + tanh(beta (1 - eta)))."""
+    return (np.tanh(beta * eta) + np.tanh(beta * (xf - eta))) / (np.tanh(beta * eta) + np.tanh(beta * (1.0 - eta)))
+
+
+def heaviside_derivative(xf, beta, eta):
+    return beta * (1.0 - np.tanh(beta * (xf - eta)) ** 2) / (np.tanh(beta * eta) + np.tanh(beta * (1.0 - eta)))
+
+
+def filter_project(x, shape, box, radius, beta, eta):
+    """Raw design x -> filtered -> projected physical field (projection inside the box only)."""
+    F = filter_weights(shape, box, radius)
+    xf = F @ np.asarray(x).reshape(-1)
+    inside = _box_mask(shape, box)
+    out = np.where(inside, heaviside(xf, beta, eta), xf)
+    return out
+
+
+def filter_project_adjoint(x, dj_dphys, shape, box, radius, beta, eta):
+    """Chain rule: dJ/dx = F^T (H'(x~) * dJ/dphys) (H' = 1 outside the box)."""
+    F = filter_weights(shape, box, radius)
+    xf = F @ np.asarray(x).reshape(-1)
+    inside = _box_mask(shape, box)
+    d = np.where(inside, heaviside_derivative(xf, beta, eta), 1.0)
+    return F.T @ (d * np.asarray(dj_dphys).reshape(-1))
+
+
+def _box_mask(shape, box):
+    nz, ny, nx = shape
+    x0, x1, y0, y1, z0, z1 = box
+    m = np.zeros(shape, bool)
+    m[z0:z1, y0:y1, x0:x1] = True
+    return m.reshape(-1)

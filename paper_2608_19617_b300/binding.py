@@ -42,6 +42,10 @@ class LbmTiming(ctypes.Structure):
                 ("lattice_updates", c_int64 * NUM_PHASES)]
 
 
+class LbmFilter(ctypes.Structure):
+    _fields_ = [("radius", c_double), ("beta", c_double), ("eta", c_double)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, func, msg):
         super().__init__(f"{func}: {status_string(status)} ({msg})")
@@ -69,6 +73,9 @@ def lib() -> ctypes.CDLL:
         "lbm_adjoint_window": (st, [c_void_p, POINTER(c_double)]),
         "lbm_design_gradient": (st, [c_void_p, c_void_p, c_size_t]),
         "lbm_set_design": (st, [c_void_p, c_void_p]),
+        "lbm_set_design_filtered": (st, [c_void_p, c_void_p, POINTER(LbmFilter)]),
+        "lbm_design_gradient_filtered": (st, [c_void_p, c_void_p, c_size_t]),
+        "lbm_get_design": (st, [c_void_p, c_void_p, c_size_t]),
         "lbm_get_state": (st, [c_void_p, c_void_p, c_size_t]),
         "lbm_set_state": (st, [c_void_p, c_void_p, c_size_t]),
         "lbm_get_adjoint_state": (st, [c_void_p, c_void_p, c_size_t]),
@@ -77,6 +84,7 @@ def lib() -> ctypes.CDLL:
         "lbm_get_timing": (st, [c_void_p, POINTER(LbmTiming)]),
         "lbm_get_counters": (st, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
         "lbm_set_graphs": (st, [c_void_p, c_int32]),
+        "lbm_set_pdl": (st, [c_void_p, c_int32]),
         "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_status_string": (ctypes.c_char_p, [c_int32]),
@@ -194,6 +202,26 @@ class Solver:
             gamma = np.ascontiguousarray(gamma.reshape(-1), dtype=np.float32)
         check(lib().lbm_set_design(self.ctx, _ptr(gamma)), "lbm_set_design")
 
+    def set_design_filtered(self, x_raw, radius=4.0, beta=2.0, eta=0.5):
+        """Design from raw variables through the density filter and Heaviside projection."""
+        if isinstance(x_raw, np.ndarray):
+            x_raw = np.ascontiguousarray(x_raw.reshape(-1), dtype=np.float32)
+        f = LbmFilter(float(radius), float(beta), float(eta))
+        check(lib().lbm_set_design_filtered(self.ctx, _ptr(x_raw), byref(f)), "lbm_set_design_filtered")
+
+    def design_gradient_filtered(self, out=None):
+        """dJ/dx for the raw variables of the last filtered design (FP64 [N])."""
+        if out is None:
+            out = np.empty(self.n, np.float64)
+        check(lib().lbm_design_gradient_filtered(self.ctx, _ptr(out), self.n), "lbm_design_gradient_filtered")
+        return out
+
+    def get_design(self, out=None):
+        if out is None:
+            out = np.empty(self.n, np.float32)
+        check(lib().lbm_get_design(self.ctx, _ptr(out), self.n), "lbm_get_design")
+        return out
+
     def get_state(self, out=None):
         if out is None:
             out = np.empty((self.q, self.n), np.float64)
@@ -225,6 +253,9 @@ class Solver:
 
     def set_graphs(self, enable: bool):
         check(lib().lbm_set_graphs(self.ctx, int(bool(enable))), "lbm_set_graphs")
+
+    def set_pdl(self, enable: bool):
+        check(lib().lbm_set_pdl(self.ctx, int(bool(enable))), "lbm_set_pdl")
 
     def counters(self):
         s, w = c_int64(), c_int64()

@@ -1,0 +1,105 @@
+// Design pre-processing of Sec. 3.3: a linear density filter of radius r over
+// the design box and the Heaviside projection of Wang et al. (2011), plus the
+// chain rule that carries dJ/dgamma back to the raw design variables.
+//
+//   x~_i  = sum_j w_ij x_j / W_i,  w_ij = max(0, r - |x_i - x_j|),  W_i = sum_j w_ij
+//           (i, j inside the design box; outside it x~ = x)
+//   gamma = H(x~) = (tanh(b eta) + tanh(b (x~ - eta))) / (tanh(b eta) + tanh(b (1 - eta)))
+//   dJ/dx_j = sum_i w_ij H'(x~_i) dJ/dgamma_i / W_i      (j inside the box)
+//
+// These run once per design update, not per time step, so they are written
+// plainly in FP64: one thread per node gathers its window.
+#pragma once
+
+#include <cstdint>
+
+namespace lbm {
+
+struct FilterGeo {
+  int nx, ny, nz;
+  int box[6];          // x0, x1, y0, y1, z0, z1 (half-open)
+  int R;               // ceil(radius)
+  double radius, beta, eta;
+  int d3;              // 1: the window extends in z
+};
+
+__device__ __forceinline__ bool in_box(const FilterGeo& f, int x, int y, int z) {
+  return x >= f.box[0] && x < f.box[1] && y >= f.box[2] && y < f.box[3] && z >= f.box[4] && z < f.box[5];
+}
+
+__device__ __forceinline__ double proj_den(const FilterGeo& f) {
+  return tanh(f.beta * f.eta) + tanh(f.beta * (1.0 - f.eta));
+}
+
+// gamma = H(filter(x)) inside the box, x outside; also stores x~ and W_i.
+__global__ void filter_project_kernel(const float* __restrict__ x, float* __restrict__ gamma, double* __restrict__ xf,
+                                      double* __restrict__ wsum, FilterGeo f) {
+  const long long n = (long long)f.nx * f.ny * f.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int X = int(i % f.nx), Y = int((i / f.nx) % f.ny), Z = int(i / ((long long)f.nx * f.ny));
+    if (!in_box(f, X, Y, Z)) {
+      gamma[i] = x[i];
+      xf[i] = double(x[i]);
+      wsum[i] = 1.0;
+      continue;
+    }
+    double s = 0.0, w = 0.0;
+    const int rz = f.d3 ? f.R : 0;
+    for (int dz = -rz; dz <= rz; ++dz)
+      for (int dy = -f.R; dy <= f.R; ++dy)
+        for (int dx = -f.R; dx <= f.R; ++dx) {
+          const int x2 = X + dx, y2 = Y + dy, z2 = Z + dz;
+          if (!in_box(f, x2, y2, z2)) continue;
+          const double wij = f.radius - sqrt(double(dx * dx + dy * dy + dz * dz));
+          if (wij <= 0.0) continue;
+          s += wij * double(x[x2 + (long long)f.nx * (y2 + (long long)f.ny * z2)]);
+          w += wij;
+        }
+    const double v = s / w;
+    xf[i] = v;
+    wsum[i] = w;
+    gamma[i] = float((tanh(f.beta * f.eta) + tanh(f.beta * (v - f.eta))) / proj_den(f));
+  }
+}
+
+// t_i = H'(x~_i) g_i / W_i inside the box (the first half of the chain rule).
+__global__ void filter_adjoint_scale_kernel(const double* __restrict__ g, const double* __restrict__ xf,
+                                            const double* __restrict__ wsum, double* __restrict__ t, FilterGeo f) {
+  const long long n = (long long)f.nx * f.ny * f.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int X = int(i % f.nx), Y = int((i / f.nx) % f.ny), Z = int(i / ((long long)f.nx * f.ny));
+    if (!in_box(f, X, Y, Z)) {
+      t[i] = 0.0;
+      continue;
+    }
+    const double th = tanh(f.beta * (xf[i] - f.eta));
+    t[i] = f.beta * (1.0 - th * th) / proj_den(f) * g[i] / wsum[i];
+  }
+}
+
+// dJ/dx_j = sum_i w_ij t_i inside the box, g_j outside (the filter is symmetric in w_ij).
+__global__ void filter_adjoint_gather_kernel(const double* __restrict__ g, const double* __restrict__ t,
+                                             double* __restrict__ out, FilterGeo f) {
+  const long long n = (long long)f.nx * f.ny * f.nz;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const int X = int(j % f.nx), Y = int((j / f.nx) % f.ny), Z = int(j / ((long long)f.nx * f.ny));
+    if (!in_box(f, X, Y, Z)) {
+      out[j] = g[j];
+      continue;
+    }
+    double s = 0.0;
+    const int rz = f.d3 ? f.R : 0;
+    for (int dz = -rz; dz <= rz; ++dz)
+      for (int dy = -f.R; dy <= f.R; ++dy)
+        for (int dx = -f.R; dx <= f.R; ++dx) {
+          const int x2 = X + dx, y2 = Y + dy, z2 = Z + dz;
+          if (!in_box(f, x2, y2, z2)) continue;
+          const double wij = f.radius - sqrt(double(dx * dx + dy * dy + dz * dz));
+          if (wij <= 0.0) continue;
+          s += wij * t[x2 + (long long)f.nx * (y2 + (long long)f.ny * z2)];
+        }
+    out[j] = s;
+  }
+}
+
+}  // namespace lbm

@@ -78,6 +78,18 @@ struct WindowAcc {
 template <class T>
 __device__ __forceinline__ T cs2() { return T(1.0 / 3.0); }
 
+// Programmatic dependent launch: a step kernel launched with programmatic
+// stream serialization may start before its predecessor finishes; it waits
+// here for the predecessor's completion (and memory) before touching any data,
+// then lets its own successor begin launching.  Without the launch attribute
+// both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
   const double t = s + x;
   if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
@@ -105,6 +117,54 @@ __device__ __forceinline__ bool on_face(const Geo& g, int x, int y, int z) {
 template <class L>
 __device__ __forceinline__ int offset(const Geo& g, int a) {
   return L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz);
+}
+
+// ---------------------------------------------------------------------------
+// Face-node table, built once on the host: everything the face kernels need
+// about a face node's neighbourhood, so that they do plain indexed loads.
+// ---------------------------------------------------------------------------
+constexpr unsigned kNone = 0xffffffffu;
+
+struct FaceTable {
+  const unsigned* __restrict__ idx;    // node index, [nface]
+  const unsigned* __restrict__ info;   // rule mask (bits 0..18: unknowns completed by a rule) | class << 24
+  const float* __restrict__ u0;        // inlet x-velocity (0 elsewhere), [nface]
+  const unsigned* __restrict__ src;    // [Q][nface]: node whose p_a becomes f_a (streaming or zero-gradient copy)
+  const unsigned* __restrict__ dst;    // [Q][nface]: node i + c_a, kNone outside the domain
+  const unsigned* __restrict__ ext;    // [Q][nface]: zero-gradient node that copied p_a(i), or kNone
+  unsigned n;                          // nface
+};
+
+// Boundary rules of Eqs. 19-21 (and the 3D velocity inlet) on the unknown
+// populations flagged in mask, in shifted form.
+template <class L, class R>
+__device__ __forceinline__ void apply_rules(R (&f)[L::Q], unsigned mask, uint8_t cls, R u0, R rho_out) {
+  if (!mask) return;
+  if (cls == WALL) {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a)
+      if (mask & (1u << a)) f[a] = (mask & (1u << L::opp(a))) ? R(0) : f[L::opp(a)];
+  } else if (cls == INLET) {
+    if (L::Q == 9) {
+      const R s = f[0] + f[2] + f[4] + R(2) * (f[3] + f[6] + f[7]);
+      const R rho = (R(1) + s) / (R(1) - u0);
+      const R ru = rho * u0;
+      f[1] = f[3] + R(2.0 / 3.0) * ru;
+      f[5] = f[7] + R(0.5) * (f[4] - f[2]) + ru * R(1.0 / 6.0);
+      f[8] = f[6] + R(0.5) * (f[2] - f[4]) + ru * R(1.0 / 6.0);
+    } else {
+#pragma unroll
+      for (int a = 0; a < L::Q; ++a)
+        if (mask & (1u << a)) f[a] = f[L::opp(a)] + R(6.0 * L::w(a) * L::cx(a)) * u0;
+    }
+  } else if (cls == OUTLET_P) {
+    const R s = f[0] + f[2] + f[4] + R(2) * (f[1] + f[5] + f[8]);
+    const R ux = (R(1) + s) / rho_out - R(1);
+    const R ru = rho_out * ux;
+    f[3] = f[1] - R(2.0 / 3.0) * ru;
+    f[6] = f[8] + R(0.5) * (f[4] - f[2]) - ru * R(1.0 / 6.0);
+    f[7] = f[5] + R(0.5) * (f[2] - f[4]) - ru * R(1.0 / 6.0);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -313,14 +373,17 @@ __device__ __forceinline__ void block_sum2(R& a, R& b) {
 // Each block keeps its own compensated FP64 window sums (j and the monitor) in
 // blk[4 b .. 4 b + 3]; thread 0 adds the block's sample.  No atomics, no
 // cross-block step: the window-end kernel reduces the blocks in a fixed order.
-__device__ __forceinline__ void sample_commit(double bj, double bm, double* blk) {
+__device__ __forceinline__ void sample_commit(double bj, double bm, double* blk, unsigned bid) {
   if (threadIdx.x == 0) {
-    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     double4 a = reinterpret_cast<double4*>(blk)[bid];
     neumaier(a.x, a.y, bj);
     neumaier(a.z, a.w, bm);
     reinterpret_cast<double4*>(blk)[bid] = a;
   }
+}
+
+__device__ __forceinline__ void sample_commit(double bj, double bm, double* blk) {
+  sample_commit(bj, bm, blk, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
 // ---------------------------------------------------------------------------
@@ -340,6 +403,7 @@ struct FwdArgs {
   int sample;                    // 1 at a sampling instant
   double* blk;                   // per-block window sums (4 doubles per block)
   int* nonfinite;
+  FaceTable ft;
 };
 
 template <class L, class R>
@@ -355,39 +419,74 @@ __device__ __forceinline__ R local_objective(const Mom<L, R>& M, const Obj<R>& o
   }
 }
 
-template <class L, class R>
-__global__ void __launch_bounds__(kBlock) fwd_step_kernel(FwdArgs<R> A) {
+// One node of a forward step (interior or face node).
+// For a face node k is its row in the face table; for an interior node k is unused.
+template <class L, class R, bool FACE>
+__device__ __forceinline__ void forward_node(const FwdArgs<R>& A, int x, int y, int z, unsigned i, unsigned k,
+                                             R& bj, R& bm) {
   const Geo& g = A.geo;
-  const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  const bool alive = x < g.nx;
-  R bj = 0, bm = 0;
-  if (alive) {
-    const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
-    const bool face = on_face<L>(g, x, y, z);
-    const uint8_t cls = face ? A.cls[i] : uint8_t(FLUID);
-    const R u0 = (face && cls == INLET) ? R(A.uin[y + g.ny * z]) : R(0);
-    R f[L::Q];
-    gather<L, R>(A.src, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f);
-    Mom<L, R> M;
-    moments<L, R>(f, A.ph, M);
-    if (!(M.rho > R(0)) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
-    const R gi = A.gfield[i];
-    R a0, B[3], T[6];
-    post_collision<L, R>(M, gi, a0, B, T);
+  R f[L::Q];
+  if (FACE) {
+    const FaceTable& t = A.ft;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
-    if (A.sample) {
-      const int* b = A.obj.box;
-      if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
-        const R w = R(A.wobj[i]);
-        if (w != R(0)) bj = w * local_objective<L, R>(M, A.obj, gi);
-      }
-      if (A.obj.mon == MON_DRAG) bm = R(-2) * gi * M.m[0];
-    }
+    for (int a = 0; a < L::Q; ++a) f[a] = A.src[a * g.n + t.src[a * t.n + k]];
+    const unsigned info = t.info[k];
+    apply_rules<L, R>(f, info & 0xffffffu, uint8_t(info >> 24), R(t.u0[k]), A.ph.rho_out);
+  } else {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) f[a] = A.src[a * g.n + i - offset<L>(g, a)];
   }
+  Mom<L, R> M;
+  moments<L, R>(f, A.ph, M);
+  if (!(M.rho > R(0)) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
+  const R gi = A.gfield[i];
+  R a0, B[3], T[6];
+  post_collision<L, R>(M, gi, a0, B, T);
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
+  if (A.sample) {
+    const int* b = A.obj.box;
+    if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
+      const R w = R(A.wobj[i]);
+      if (w != R(0)) bj = w * local_objective<L, R>(M, A.obj, gi);
+    }
+    if (A.obj.mon == MON_DRAG) bm = R(-2) * gi * M.m[0];
+  }
+}
+
+// Interior nodes: x in [1, nx-1), y in [1, ny-1), z in [1, nz-1) (3D).  No
+// face logic at all, so the instruction stream stays short.
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
+  pdl_enter();
+  const Geo& g = A.geo;
+  const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
+  const int z = L::D == 3 ? 1 + int(blockIdx.z) : 0;
+  R bj = 0, bm = 0;
+  if (x < g.nx - 1)
+    forward_node<L, R, false>(A, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
   if (A.sample) {   // uniform across the grid
     block_sum2<R>(bj, bm);
-    sample_commit(double(bj), double(bm), A.blk);
+    sample_commit(double(bj), double(bm), A.blk,
+                  blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+  }
+}
+
+// Face nodes, from the list face[0..nface); block sums after the interior's.
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned blk0) {
+  pdl_enter();
+  const Geo& g = A.geo;
+  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
+  R bj = 0, bm = 0;
+  if (k < A.ft.n) {
+    const unsigned i = A.ft.idx[k];
+    const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
+    forward_node<L, R, true>(A, x, y, z, i, k, bj, bm);
+  }
+  if (A.sample) {
+    block_sum2<R>(bj, bm);
+    sample_commit(double(bj), double(bm), A.blk, blk0 + blockIdx.x);
   }
 }
 
@@ -409,16 +508,20 @@ __global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, in
     neumaier(sm, cm, a.w);
     reinterpret_cast<double4*>(blk)[b] = make_double4(0.0, 0.0, 0.0, 0.0);
   }
-  sh[0][threadIdx.x] = sj; sh[1][threadIdx.x] = cj; sh[2][threadIdx.x] = sm; sh[3][threadIdx.x] = cm;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  double tj = 0, tcj = 0, tm = 0, tcm = 0;
-  for (int t = 0; t < kEndThreads; ++t) {
-    neumaier(tj, tcj, sh[0][t]);
-    neumaier(tj, tcj, sh[1][t]);
-    neumaier(tm, tcm, sh[2][t]);
-    neumaier(tm, tcm, sh[3][t]);
+  // Fixed-shape tree over the threads' (sum, compensation) pairs: deterministic.
+  const int t = threadIdx.x;
+  sh[0][t] = sj; sh[1][t] = cj; sh[2][t] = sm; sh[3][t] = cm;
+  for (int stride = kEndThreads / 2; stride > 0; stride >>= 1) {
+    __syncthreads();
+    if (t < stride) {
+      neumaier(sh[0][t], sh[1][t], sh[0][t + stride]);
+      sh[1][t] += sh[1][t + stride];
+      neumaier(sh[2][t], sh[3][t], sh[2][t + stride]);
+      sh[3][t] += sh[3][t + stride];
+    }
   }
+  if (t != 0) return;
+  const double tj = sh[0][0], tcj = sh[1][0], tm = sh[2][0], tcm = sh[3][0];
   const double jm = (tj + tcj) / nsamples + jconst;
   const double mm = mon_kind == MON_DRAG ? (tm + tcm) / nsamples * mon_scale : jm;
   if (acc->has_prev) {
@@ -460,11 +563,12 @@ struct AdjArgs {
   int sample;
   int terminal;                  // 1: b^{n+1} = 0 (last step of the window)
   int dbox[6];                   // design box
+  FaceTable ft;
 };
 
 // Transposed boundary completion at a face node (in place on b).
 template <class L, class R>
-__device__ __noinline__ void bc_transpose(R* b, unsigned unk, uint8_t cls, R u0) {
+__device__ __forceinline__ void bc_transpose(R (&b)[L::Q], unsigned unk, uint8_t cls, R u0) {
   if (!unk) return;
   if (cls == WALL) {
 #pragma unroll
@@ -562,27 +666,47 @@ __global__ void __launch_bounds__(kBlock) adj_pull_kernel(const R* __restrict__ 
   for (int k = 0; k < L::Q; ++k) out[k * g.n + i] = a[k];
 }
 
-template <class L, class R>
-__global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
+// One node of an adjoint step (interior or face node).
+template <class L, class R, bool FACE>
+__device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, int x, int y, int z, unsigned i, unsigned kf) {
   const Geo& g = A.geo;
-  const int x = blockIdx.x * kBlock + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  if (x >= g.nx) return;
-  const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
-  const bool face = on_face<L>(g, x, y, z);
-  const uint8_t cls = face ? A.cls[i] : uint8_t(FLUID);
-  const R u0 = (face && cls == INLET) ? R(A.uin[y + g.ny * z]) : R(0);
+  const FaceTable& ft = A.ft;
+  const unsigned info = FACE ? ft.info[kf] : 0u;
+  const uint8_t cls = uint8_t(info >> 24);
+  const unsigned mask = info & 0xffffffu;
+  const R u0 = FACE ? R(ft.u0[kf]) : R(0);
 
   // Weighted moments of the pulled adjoint a^n: A0 = sum w a, A1 = sum w c a,
   // A2 = sum w c c a.  Everything below needs a only through them.
   R A0, A1[3], A2[6];
   {
     R a[L::Q];
-    pull_adjoint<L, R>(A.terminal ? nullptr : A.bnext, A.cls, g, x, y, z, i, face, a);
+    if (A.terminal) {
+#pragma unroll
+      for (int k = 0; k < L::Q; ++k) a[k] = R(0);
+    } else if (FACE) {
+#pragma unroll
+      for (int k = 0; k < L::Q; ++k) {
+        const unsigned d = ft.dst[k * ft.n + kf], e = ft.ext[k * ft.n + kf];
+        a[k] = d != kNone ? A.bnext[k * g.n + d] : R(0);
+        if (e != kNone) a[k] += A.bnext[k * g.n + e];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < L::Q; ++k) a[k] = A.bnext[k * g.n + i + offset<L>(g, k)];
+    }
     raw_moments<L, R, true>(a, A0, A1, A2);
   }
 
   R f[L::Q];
-  const unsigned unk = gather<L, R>(A.pprev, g, x, y, z, i, face, cls, u0, A.ph.rho_out, f);
+  if (FACE) {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) f[a] = A.pprev[a * g.n + ft.src[a * ft.n + kf]];
+    apply_rules<L, R>(f, mask, cls, u0, A.ph.rho_out);
+  } else {
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) f[a] = A.pprev[a * g.n + i - offset<L>(g, a)];
+  }
   Mom<L, R> M;
   moments<L, R>(f, A.ph, M);
   const R gi = A.gfield[i];
@@ -682,19 +806,33 @@ __global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
   R b[L::Q];
 #pragma unroll
   for (int k = 0; k < L::Q; ++k) b[k] = quad_form<L, R>(k, grho, gm, cpi);
-  if (face) {
-    R t[L::Q];
-#pragma unroll
-    for (int k = 0; k < L::Q; ++k) t[k] = b[k];
-    bc_transpose<L, R>(t, unk, cls, u0);
-#pragma unroll
-    for (int k = 0; k < L::Q; ++k) b[k] = t[k];
-  }
+  if (FACE) bc_transpose<L, R>(b, mask, cls, u0);
 #pragma unroll
   for (int k = 0; k < L::Q; ++k) A.bout[k * g.n + i] = b[k];
 
   const int* d = A.dbox;
   if (x >= d[0] && x < d[1] && y >= d[2] && y < d[3] && z >= d[4] && z < d[5]) A.gpart[i] += gt;
+}
+
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) adj_interior_kernel(AdjArgs<R> A) {
+  pdl_enter();
+  const Geo& g = A.geo;
+  const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
+  const int z = L::D == 3 ? 1 + int(blockIdx.z) : 0;
+  if (x >= g.nx - 1) return;
+  adjoint_node<L, R, false>(A, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u);
+}
+
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) adj_face_kernel(AdjArgs<R> A) {
+  pdl_enter();
+  const Geo& g = A.geo;
+  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
+  if (k >= A.ft.n) return;
+  const unsigned i = A.ft.idx[k];
+  const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
+  adjoint_node<L, R, true>(A, x, y, z, i, k);
 }
 
 // Fold a segment's sensitivity partials into the FP64 (sum, compensation)

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "lbmadj.h"
+#include "filter.cuh"
 #include "kernels.cuh"
 
 namespace {
@@ -76,8 +77,11 @@ unsigned mask_with_cx(int sx) {
 // Layout of the caller's workspace.
 struct Layout {
   size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gpart, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
-      partials, acc, flags, total;
+      partials, acc, flags, f_idx, f_info, f_u0, f_src, f_dst, f_ext, xraw, xfilt, wfilt, total;
   int nblocks_fwd, nblocks_1d, nslots;
+  int igx, igy, igz;          // interior grid (blocks of kBlock along x)
+  unsigned nface;             // face nodes
+  int face_blocks;
   bool stage_in_seg;
 };
 
@@ -125,7 +129,15 @@ Layout make_layout(const lbm_config& c) {
   const int d = c.lattice == LBM_D2Q9 ? 2 : 3;
   const size_t rs = c.precision == LBM_FP64 ? 8 : 4;
   const size_t lat = align_up(size_t(q) * n * rs);
-  L.nblocks_fwd = ((c.nx + lbm::kBlock - 1) / lbm::kBlock) * c.ny * c.nz;
+  // Interior nodes (off every face) run in one kernel, face nodes in another.
+  const int ix = c.nx > 2 ? c.nx - 2 : 0, iy = c.ny > 2 ? c.ny - 2 : 0;
+  const int iz = c.lattice == LBM_D2Q9 ? 1 : (c.nz > 2 ? c.nz - 2 : 0);
+  L.igx = (ix + lbm::kBlock - 1) / lbm::kBlock;
+  L.igy = iy;
+  L.igz = iz;
+  L.nface = unsigned(n - size_t(ix) * iy * iz);
+  L.face_blocks = int((L.nface + lbm::kBlock - 1) / lbm::kBlock);
+  L.nblocks_fwd = L.igx * L.igy * L.igz + L.face_blocks;
   L.nblocks_1d = int((n + lbm::kBlock - 1) / lbm::kBlock);
   L.nslots = c.window_len / c.ckpt_every;
   const bool native = c.ckpt_format == LBM_CKPT_NATIVE;
@@ -148,6 +160,15 @@ Layout make_layout(const lbm_config& c) {
   L.gpart = take(n * rs);
   L.gout = take(n * 8);
   L.partials = take(size_t(L.nblocks_fwd) * 32);
+  L.f_idx = take(size_t(L.nface) * 4);
+  L.f_info = take(size_t(L.nface) * 4);
+  L.f_u0 = take(size_t(L.nface) * 4);
+  L.f_src = take(size_t(L.nface) * 4 * q);
+  L.f_dst = take(size_t(L.nface) * 4 * q);
+  L.f_ext = take(size_t(L.nface) * 4 * q);
+  L.xraw = take(n * 4);       // raw design variables (filtered designs)
+  L.xfilt = take(n * 8);      // filtered field x~
+  L.wfilt = take(n * 8);      // filter normalisation W_i
   L.acc = take(sizeof(lbm::WindowAcc));
   L.flags = take(16);
   L.ckpt = take(L.ckpt_slot * L.nslots);
@@ -196,7 +217,10 @@ struct lbm_ctx {
   cudaStream_t stream;        // the caller's stream: everything runs in its order
   cudaStream_t ls = nullptr;  // stream launches go to (the capture stream while capturing)
   cudaStream_t cap = nullptr; // private stream used only to capture graphs
+  cudaStream_t side = nullptr;            // face kernels run here, forked from ls and joined back
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool use_graphs = true;
+  bool use_pdl = false;
   bool capturing = false;
   std::vector<Pending>* sink = nullptr;   // where end() files events while capturing
   GraphRec gwin[2][2];        // forward window graphs by [start parity][timing]
@@ -212,6 +236,8 @@ struct lbm_ctx {
   double jconst = 0;
   bool timing = false;
   int64_t timing_failures = 0;
+  bool filtered = false;      // design set through lbm_set_design_filtered
+  lbm::FilterGeo fgeo{};
   lbm_timing tm{};
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
@@ -294,6 +320,9 @@ struct lbm_ctx {
     for (auto& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
     for (auto e : pool) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
+    if (side) cudaStreamDestroy(side);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
   }
 };
 
@@ -308,6 +337,46 @@ struct ImplT final : Impl {
   int flat_blocks() const {
     long long b = (long long)(c->n * c->q + 255) / 256;
     return int(b < 148 * 32 ? b : 148 * 32);
+  }
+  dim3 igrid() const { return dim3(c->lay.igx, c->lay.igy, c->lay.igz); }
+  lbm::FaceTable table() const {
+    return lbm::FaceTable{c->template at<unsigned>(c->lay.f_idx), c->template at<unsigned>(c->lay.f_info),
+                          c->template at<float>(c->lay.f_u0),   c->template at<unsigned>(c->lay.f_src),
+                          c->template at<unsigned>(c->lay.f_dst), c->template at<unsigned>(c->lay.f_ext),
+                          c->lay.nface};
+  }
+  bool has_interior() const { return c->lay.igx > 0 && c->lay.igy > 0 && c->lay.igz > 0; }
+  // Step kernels: optionally with programmatic stream serialization, so that a
+  // launch overlaps the tail of its predecessor (the kernel waits in
+  // pdl_enter before touching data).
+  template <class... Args>
+  void launch(void (*kernel)(Args...), dim3 grid, cudaStream_t st, Args... args) {
+    if (c->use_pdl) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = dim3(lbm::kBlock);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, kernel, args...);
+    } else {
+      kernel<<<grid, lbm::kBlock, 0, st>>>(args...);
+    }
+  }
+  // Interior kernel on the launch stream, face kernel on the side stream,
+  // forked and joined with events so that both run concurrently (and become
+  // parallel branches when captured into a graph).
+  template <class IK, class FK>
+  void fork_join(IK interior, FK face) {
+    cudaEventRecord(c->fork_ev, c->ls);
+    cudaStreamWaitEvent(c->side, c->fork_ev, 0);
+    face(c->side);
+    if (has_interior()) interior(c->ls);
+    cudaEventRecord(c->join_ev, c->side);
+    cudaStreamWaitEvent(c->ls, c->join_ev, 0);
   }
   lbm::Phys<R> phys() const { return {R(c->cfg.tau), R(c->cfg.cs_smag * c->cfg.cs_smag), R(c->cfg.rho_out)}; }
   lbm::Obj<R> obj() const {
@@ -335,7 +404,10 @@ struct ImplT final : Impl {
     A.sample = sample;
     A.blk = c->template at<double>(c->lay.partials);
     A.nonfinite = c->template at<int>(c->lay.flags);
-    lbm::fwd_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(A);
+    A.ft = table();
+    const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
+    fork_join([&](cudaStream_t st) { launch(lbm::fwd_interior_kernel<L, R>, igrid(), st, A); },
+              [&](cudaStream_t st) { launch(lbm::fwd_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A, blk0); });
   }
   void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
     lbm::AdjArgs<R> A;
@@ -353,7 +425,9 @@ struct ImplT final : Impl {
     A.sample = sample;
     A.terminal = bnext == nullptr;
     for (int i = 0; i < 6; ++i) A.dbox[i] = c->cfg.design_box[i];
-    lbm::adj_step_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(A);
+    A.ft = table();
+    fork_join([&](cudaStream_t st) { launch(lbm::adj_interior_kernel<L, R>, igrid(), st, A); },
+              [&](cudaStream_t st) { launch(lbm::adj_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A); });
   }
   void pull(const void* b, void* out) override {
     lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(
@@ -535,6 +609,83 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
   return LBM_OK;
 }
 
+// The face table: for each face node (ascending index) its class, the mask of
+// unknowns completed by a rule, its inlet velocity, and per direction a the
+// node whose p_a becomes f_a (the upstream neighbour, or for a zero-gradient
+// outlet the neighbour's upstream node), the downstream node i + c_a, and the
+// zero-gradient node that copied p_a(i).
+template <class L>
+lbm_status build_face_table(lbm_ctx* c, const uint8_t* cls, const float* inlet_u) {
+  const lbm_config& k = c->cfg;
+  const Layout& lay = c->lay;
+  const unsigned nf = lay.nface;
+  if (nf == 0) return LBM_OK;
+  std::vector<float> uin(size_t(k.ny) * k.nz, 0.f);
+  if (inlet_u) {
+    CUDA_TRY(cudaMemcpy(uin.data(), inlet_u, uin.size() * 4, cudaMemcpyDefault));
+  }
+  std::vector<unsigned> idx, info, src(size_t(L::Q) * nf), dst(size_t(L::Q) * nf), ext(size_t(L::Q) * nf);
+  std::vector<float> u0;
+  idx.reserve(nf);
+  info.reserve(nf);
+  u0.reserve(nf);
+  const bool d3 = L::D == 3;
+  const int dims[3] = {k.nx, k.ny, k.nz};
+  auto nb = [&](int x, int y, int z, int dx, int dy, int dz, unsigned& j) {
+    int p[3] = {x + dx, y + dy, z + dz};
+    for (int a = 0; a < 3; ++a) {
+      if (p[a] < 0 || p[a] >= dims[a]) {
+        if (!k.periodic[a]) return false;
+        p[a] = (p[a] + dims[a]) % dims[a];
+      }
+    }
+    j = unsigned(p[0]) + unsigned(k.nx) * (unsigned(p[1]) + unsigned(k.ny) * unsigned(p[2]));
+    return true;
+  };
+  for (int z = 0; z < k.nz; ++z)
+    for (int y = 0; y < k.ny; ++y)
+      for (int x = 0; x < k.nx; ++x) {
+        if (!(x == 0 || x == k.nx - 1 || y == 0 || y == k.ny - 1 || (d3 && (z == 0 || z == k.nz - 1)))) continue;
+        const unsigned i = unsigned(x) + unsigned(k.nx) * (unsigned(y) + unsigned(k.ny) * unsigned(z));
+        const unsigned r = unsigned(idx.size());
+        const uint8_t kind = cls[i];
+        unsigned mask = 0;
+        for (int a = 0; a < L::Q; ++a) {
+          unsigned j;
+          if (nb(x, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j)) {
+            src[size_t(a) * nf + r] = j;
+          } else if (kind == LBM_OUTLET_ZEROGRAD) {
+            const int xn = x == k.nx - 1 ? x - 1 : x + 1;
+            if (!nb(xn, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j)) return fail(LBM_ERR_ARG, "zero-gradient source outside");
+            src[size_t(a) * nf + r] = j;
+          } else {
+            src[size_t(a) * nf + r] = i;   // overwritten by the rule
+            mask |= 1u << a;
+          }
+          dst[size_t(a) * nf + r] = nb(x, y, z, L::cx(a), L::cy(a), L::cz(a), j) ? j : lbm::kNone;
+          unsigned e = lbm::kNone;
+          if ((x == k.nx - 1 && L::cx(a) == -1) || (x == 0 && L::cx(a) == 1)) {
+            if (nb(x, y, z, 0, L::cy(a), L::cz(a), j) && cls[j] == LBM_OUTLET_ZEROGRAD) e = j;
+          }
+          ext[size_t(a) * nf + r] = e;
+        }
+        if (kind == LBM_FLUID) mask = 0;
+        idx.push_back(i);
+        info.push_back(mask | (unsigned(kind) << 24));
+        u0.push_back(kind == LBM_INLET ? uin[size_t(y) + size_t(k.ny) * z] : 0.f);
+      }
+  if (idx.size() != nf) return fail(LBM_ERR_ARG, "face count mismatch");
+  cudaStream_t s = c->stream;
+  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_idx), idx.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_info), info.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_u0), u0.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_src), src.data(), src.size() * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_dst), dst.data(), dst.size() * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_ext), ext.data(), ext.size() * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return LBM_OK;
+}
+
 // Record body() into a CUDA graph on the private capture stream and
 // instantiate it.  The caller's stream may be the legacy default stream,
 // which cannot be captured; the graph is launched into it afterwards.
@@ -621,6 +772,9 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
                       unsigned(c.nx), unsigned(c.nx) * unsigned(c.ny)};
   ctx->cur = 0;
   lbm_ctx* x = ctx.get();
+  CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
   if (c.lattice == LBM_D2Q9) {
     if (c.precision == LBM_FP32) ctx->impl.reset(new ImplT<D2Q9, float>(x));
     else ctx->impl.reset(new ImplT<D2Q9, double>(x));
@@ -635,6 +789,8 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   CUDA_TRY(cudaMemsetAsync(x->at(lay.acc), 0, sizeof(lbm::WindowAcc), s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.flags), 0, 16, s));
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.cls), node_class, n, cudaMemcpyDefault, s));
+  if (c.lattice == LBM_D2Q9) LBM_TRY(build_face_table<D2Q9>(x, node_class, inlet_u));
+  else LBM_TRY(build_face_table<D3Q19>(x, node_class, inlet_u));
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.gamma), design_gamma, n * 4, cudaMemcpyDefault, s));
   if (objective_weights) CUDA_TRY(cudaMemcpyAsync(x->at(lay.wobj), objective_weights, n * 4, cudaMemcpyDefault, s));
   else CUDA_TRY(cudaMemsetAsync(x->at(lay.wobj), 0, n * 4, s));
@@ -759,12 +915,69 @@ lbm_status lbm_design_gradient(lbm_ctx* c, double* grad, size_t n) {
 lbm_status lbm_set_design(lbm_ctx* c, const float* gamma) {
   if (!c || !gamma) return fail(LBM_ERR_ARG, "null argument");
   CUDA_TRY(cudaMemcpyAsync(c->at(c->lay.gamma), gamma, c->n * 4, cudaMemcpyDefault, c->stream));
+  c->filtered = false;
   c->impl->set_design();
   CUDA_TRY(cudaGetLastError());
   c->window_valid = false;
   c->grad_valid = false;
   c->nwin_for_ratio = 0;
   return check_flags(c, 1, LBM_ERR_ARG, "design values must lie in [0, 1]");
+}
+
+lbm_status lbm_get_design(lbm_ctx* c, float* gamma, size_t n) {
+  if (!c || !gamma) return fail(LBM_ERR_ARG, "null argument");
+  if (n != c->n) return fail(LBM_ERR_ARG, "design length %zu, expected %zu", n, c->n);
+  CUDA_TRY(cudaMemcpyAsync(gamma, c->at(c->lay.gamma), n * 4, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_design_filtered(lbm_ctx* c, const float* x_raw, const lbm_filter* f) {
+  if (!c || !x_raw || !f) return fail(LBM_ERR_ARG, "null argument");
+  if (!(f->radius > 0.0 && f->radius < 64.0)) return fail(LBM_ERR_ARG, "filter radius must be in (0, 64)");
+  if (!(f->beta > 0.0) || !(f->eta > 0.0 && f->eta < 1.0))
+    return fail(LBM_ERR_ARG, "projection needs beta > 0 and 0 < eta < 1");
+  lbm::FilterGeo g{};
+  g.nx = c->cfg.nx;
+  g.ny = c->cfg.ny;
+  g.nz = c->cfg.nz;
+  for (int k = 0; k < 6; ++k) g.box[k] = c->cfg.design_box[k];
+  g.R = int(std::ceil(f->radius));
+  g.radius = f->radius;
+  g.beta = f->beta;
+  g.eta = f->eta;
+  g.d3 = c->cfg.lattice == LBM_D3Q19;
+  CUDA_TRY(cudaMemcpyAsync(c->at(c->lay.xraw), x_raw, c->n * 4, cudaMemcpyDefault, c->stream));
+  const long long blocks = (long long)(c->n + 255) / 256;
+  lbm::filter_project_kernel<<<int(blocks < 148 * 32 ? blocks : 148 * 32), 256, 0, c->stream>>>(
+      c->at<float>(c->lay.xraw), c->at<float>(c->lay.gamma), c->at<double>(c->lay.xfilt), c->at<double>(c->lay.wfilt), g);
+  c->impl->set_design();
+  CUDA_TRY(cudaGetLastError());
+  c->window_valid = false;
+  c->grad_valid = false;
+  c->nwin_for_ratio = 0;
+  c->filtered = true;
+  c->fgeo = g;
+  return check_flags(c, 1, LBM_ERR_ARG, "raw design values must lie in [0, 1]");
+}
+
+lbm_status lbm_design_gradient_filtered(lbm_ctx* c, double* grad, size_t n) {
+  if (!c || !grad) return fail(LBM_ERR_ARG, "null argument");
+  if (!c->grad_valid) return fail(LBM_ERR_STATE, "no adjoint window computed");
+  if (!c->filtered) return fail(LBM_ERR_STATE, "the design was not set through lbm_set_design_filtered");
+  if (n != c->n) return fail(LBM_ERR_ARG, "gradient length %zu, expected %zu", n, c->n);
+  c->impl->grad();
+  double* t = c->at<double>(c->lay.stage);
+  double* out = t + c->n;
+  const long long blocks = (long long)(c->n + 255) / 256;
+  const int nb = int(blocks < 148 * 32 ? blocks : 148 * 32);
+  lbm::filter_adjoint_scale_kernel<<<nb, 256, 0, c->stream>>>(c->at<double>(c->lay.gout), c->at<double>(c->lay.xfilt),
+                                                               c->at<double>(c->lay.wfilt), t, c->fgeo);
+  lbm::filter_adjoint_gather_kernel<<<nb, 256, 0, c->stream>>>(c->at<double>(c->lay.gout), t, out, c->fgeo);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(grad, out, n * 8, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
 }
 
 lbm_status lbm_get_state(lbm_ctx* c, double* f, size_t n) {
@@ -839,6 +1052,17 @@ lbm_status lbm_get_timing(lbm_ctx* c, lbm_timing* out) {
 lbm_status lbm_set_graphs(lbm_ctx* c, int32_t enable) {
   if (!c) return fail(LBM_ERR_ARG, "null context");
   c->use_graphs = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_pdl(lbm_ctx* c, int32_t enable) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if ((enable != 0) != c->use_pdl) {
+    // captured graphs hold the old launch attributes: capture again on next use
+    for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);
+    for (auto& g : c->gadj) c->drop_graph(g);
+  }
+  c->use_pdl = enable != 0;
   return LBM_OK;
 }
 

@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--spinup-windows", type=int, default=4)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--graphs", type=int, default=1, help="replay windows / sweeps as CUDA graphs")
+    ap.add_argument("--pipeline", type=int, default=1,
+                    help="recompute the next segment while the adjoint sweeps the current one")
     ap.add_argument("--pdl", type=int, default=0, help="programmatic dependent launch of the step kernels")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: no CPU baseline, no FP64 check, no e2e pass")
@@ -193,6 +195,18 @@ def whole_job_mlups(lus_per_step_per_rank, steps, world, ms_max):
     return world * steps * lus_per_step_per_rank / (ms_max / 1e3) / 1e6
 
 
+def unit_traffic(unit, case, K):
+    """ncu DRAM bytes of one unit of work, from profiles/traffic.json (None if
+    any kernel involved has no capture for the current source)."""
+    fwd = [measured_traffic(k, case.name) for k in ("fwd_interior_kernel", "fwd_face_kernel")]
+    adj = [measured_traffic(k, case.name) for k in ("adj_interior_kernel", "adj_face_kernel")]
+    if unit == "forward step":
+        return None if None in fwd else sum(fwd)
+    if None in fwd or None in adj:
+        return None
+    return sum(adj) + sum(fwd) * (K - 1) / K
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -287,7 +301,7 @@ def run_ours(args, case, rank, world, local):
     stream = torch.cuda.Stream()
     prec = B.LBM_FP64 if args.precision == "fp64" else B.LBM_FP32
     with torch.cuda.stream(stream):
-        sol = B.Solver(case, prec, stream=stream)
+        sol = B.Solver(case, prec, stream=stream, pipeline=int(args.pipeline))
     sol.set_graphs(bool(args.graphs))
     sol.set_pdl(bool(args.pdl))
     n = case.n
@@ -296,22 +310,31 @@ def run_ours(args, case, rank, world, local):
     grad_dev = torch.empty(n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (126 MB)
 
-    def one_step():
+    sweep_ev = []     # CUDA events around each timed adjoint sweep (library stream)
+
+    def one_step(timed=False):
         sol.step_window()
         sol.window_converged()
+        if timed:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
         sol.adjoint_window()
+        if timed:
+            b.record(stream)
+            sweep_ev.append((a, b))
         sol.design_gradient(grad_dev)
 
     # spin-up so that the timed windows see a developed flow
     sol.advance(args.spinup_windows * W)
+    # Phase timing is on from the first warm-up step: the graphs that carry its
+    # event nodes are captured and instantiated there, outside the timed region.
+    sol.set_timing(True)
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-
-    sol.set_timing(True)
-    sol.get_timing()
+    sol.get_timing()          # reset the phase counters
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -319,7 +342,7 @@ def run_ours(args, case, rank, world, local):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xff)
                 ev[k][0].record(stream)
-                one_step()
+                one_step(timed=True)
                 ev[k][1].record(stream)
         torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -352,24 +375,41 @@ def run_ours(args, case, rank, world, local):
 
     pk, pk_kind = peaks()
     hbm = float(pk["hbm_gbs"])
+    rs = 8 if prec == B.LBM_FP64 else 4
     phase_rows = {}
     for ph in ("forward", "recompute", "adjoint"):
         t = timing[ph]
         if t["launches"]:
             avg_ms = t["ms"] / t["launches"]
-            bpl = bytes_per_lu(case, ph, rs=8 if prec == B.LBM_FP64 else 4) * n
+            bpl = bytes_per_lu(case, ph, rs=rs) * n
             phase_rows[ph] = {"steps": t["launches"], "ms": t["ms"], "avg_step_us": 1e3 * avg_ms,
-                              "bytes_per_launch": bpl, "gbs": bpl / (avg_ms / 1e3) / 1e9}
-    dom = max(phase_rows, key=lambda p: phase_rows[p]["ms"])
-    kname = {"forward": "fwd_interior_kernel+fwd_face_kernel", "recompute": "fwd_interior_kernel+fwd_face_kernel",
-             "adjoint": "adj_interior_kernel+adj_face_kernel"}[dom]
-    ach = phase_rows[dom]["gbs"]
+                              "bytes_per_step": bpl, "gbs": bpl / (avg_ms / 1e3) / 1e9}
+    # Units of the roofline: a forward step, and an adjoint-sweep
+    # step = one adjoint step plus its share (K-1)/K of a recompute step.  The
+    # sweep is timed whole (events around lbm_adjoint_window), since recompute
+    # and adjoint steps may run concurrently.
+    sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / len(sweep_ev)
+    sweep_b = (bytes_per_lu(case, "adjoint", rs=rs) + bytes_per_lu(case, "recompute", rs=rs) * (K - 1) / K) * n
+    units = {
+        "forward step": {"bytes": bytes_per_lu(case, "forward", rs=rs) * n,
+                         "us": phase_rows["forward"]["avg_step_us"],
+                         "kernel": "fwd_interior_kernel+fwd_face_kernel",
+                         "total_ms": phase_rows["forward"]["ms"] / args.steps},
+        "adjoint sweep step": {"bytes": sweep_b, "us": 1e3 * sweep_ms / W,
+                               "kernel": "adj_interior_kernel+adj_face_kernel with fwd_interior_kernel+fwd_face_kernel recompute",
+                               "total_ms": sweep_ms},
+    }
+    dom = max(units, key=lambda u: units[u]["total_ms"])
+    u = units[dom]
+    ach = u["bytes"] / (u["us"] / 1e6) / 1e9
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": measured_traffic(kname, case.name), "kernel": kname, "phase": dom,
-            "timing": "CUDA events around each phase's back-to-back steps on the library stream; "
-                      "one step = the concurrent interior and face kernels",
+            "traffic": unit_traffic(dom, case, K),
+            "unit_of_work": dom, "kernel": u["kernel"], "bytes_per_unit": u["bytes"], "us_per_unit": u["us"],
             "peak_kind": f"{pk_kind} hbm_gbs (copy)",
-            "bytes_per_lu": bytes_per_lu(case, dom, rs=8 if prec == B.LBM_FP64 else 4), "phases": phase_rows}
+            "timing": "CUDA events on the library stream inside the timed region: per forward-window phase, and "
+                      "around each whole adjoint sweep",
+            "units": {k: {"us": v["us"], "gbs": v["bytes"] / (v["us"] / 1e6) / 1e9} for k, v in units.items()},
+            "phases": phase_rows}
 
     # Accuracy beside the number: the FP32 window and adjoint against the FP64
     # GPU path (native checkpoints) from the same start field.  The FP64
@@ -417,7 +457,8 @@ def run_ours(args, case, rank, world, local):
                "cpu": cpu_model()}
 
     # each step is an interior and a face kernel; plus window end, folds, gradient, codecs
-    launches_per_step = 2 * W + 1 + 2 * (W - S) + 2 * W + S + 1 + (2 * S if case.ckpt_format else 0)
+    launches_per_step = (2 * W + (2 if case.lattice == 9 else 1) + 2 * (W - S) + 2 * W + S + 1
+                         + (2 * S if case.ckpt_format else 0))
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -428,12 +469,11 @@ def run_ours(args, case, rank, world, local):
                    "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
                    "ckpt_format": ["fp32", "fp16", "bf16"][case.ckpt_format], "tau": case.tau,
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
-                   "cuda_graphs": bool(args.graphs), "pdl": bool(args.pdl),
+                   "cuda_graphs": bool(args.graphs), "pipeline": bool(args.pipeline), "pdl": bool(args.pdl),
                    "l2": "flushed (256 MB write) before every timed step; inside a step the forward "
                          "lattices (19 MB) stay L2-resident"},
         "fwd_mlups": 1e-6 * timing["forward"]["lattice_updates"] / (timing["forward"]["ms"] / 1e3),
-        "adj_mlups_incl_recompute": 1e-6 * timing["adjoint"]["lattice_updates"] /
-            ((timing["adjoint"]["ms"] + timing["recompute"]["ms"] + timing["checkpoint"]["ms"]) / 1e3),
+        "adj_mlups_incl_recompute": 1e-6 * W * n / (sweep_ms / 1e3),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": (None if e2e_value is None else

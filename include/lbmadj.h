@@ -85,7 +85,8 @@ enum { LBM_CKPT_NATIVE = 0, LBM_CKPT_FP16 = 1, LBM_CKPT_BF16 = 2 };
 
 typedef struct {
   int32_t lattice;          /* LBM_D2Q9 or LBM_D3Q19                                  */
-  int32_t nx, ny, nz;       /* lattice size; nz = 1 for D2Q9                          */
+  int32_t nx, ny, nz;       /* lattice size; for D2Q9, nz > 1 stacks nz independent 2D
+                               lattices (a batch of replicas: c_z = 0, slices never mix) */
   int32_t precision;        /* LBM_FP32 or LBM_FP64 (populations and adjoint)          */
   int32_t periodic[3];      /* 1 = periodic along x / y / z                           */
   double tau;               /* molecular relaxation time, nu = (tau - 1/2)/3 (Eq. 8)  */
@@ -105,6 +106,8 @@ typedef struct {
   int32_t ckpt_format;      /* LBM_CKPT_*                                             */
   int32_t obj_box[6];       /* x0,x1,y0,y1,z0,z1 (half-open): weights read only here  */
   int32_t design_box[6];    /* x0,x1,y0,y1,z0,z1 (half-open): gradient nonzero only here */
+  int32_t pipeline;         /* 1: recompute segment s-1 while the adjoint sweeps segment s
+                               (twice the segment buffer); 0: one after the other        */
 } lbm_config;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -144,6 +147,14 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
  * Errors: LBM_ERR_NONFINITE (the window produced rho <= 0 or NaN/Inf; the
  * window is not recorded), LBM_ERR_CUDA. */
 lbm_status lbm_step_window(lbm_ctx* ctx, double* J_window, double* monitor_window);
+
+/* Window means of the objective and monitor of every slice of a D2Q9 batch
+ * (nz independent 2D lattices) for the last completed window; J and monitor
+ * are host arrays of nslices = nz doubles (monitor may be NULL).  The
+ * gradient of lbm_design_gradient at slice s is dJ_s/dgamma_s, since the
+ * slices are independent.  Errors: LBM_ERR_ARG for D3Q19 or nslices != nz,
+ * LBM_ERR_STATE before a window. */
+lbm_status lbm_window_objectives(lbm_ctx* ctx, double* J, double* monitor, size_t nslices);
 
 /* Consecutive-window test of Eq. 26 between the last two windows:
  * ratio = |(M_i - M_{i-1}) / M_i| (absolute difference when |M_i| < 1e-30),

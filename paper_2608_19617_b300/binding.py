@@ -33,7 +33,7 @@ class LbmConfig(ctypes.Structure):
         ("objective_uref", c_double * 3), ("monitor_u", c_double), ("monitor_l", c_double),
         ("window_len", c_int32), ("sample_every", c_int32), ("conv_tol", c_double),
         ("ckpt_every", c_int32), ("ckpt_format", c_int32),
-        ("obj_box", c_int32 * 6), ("design_box", c_int32 * 6),
+        ("obj_box", c_int32 * 6), ("design_box", c_int32 * 6), ("pipeline", c_int32),
     ]
 
 
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
                             c_void_p, POINTER(c_void_p)]),
         "lbm_step_window": (st, [c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_window_converged": (st, [c_void_p, POINTER(c_int32), POINTER(c_double)]),
+        "lbm_window_objectives": (st, [c_void_p, c_void_p, c_void_p, c_size_t]),
         "lbm_adjoint_window": (st, [c_void_p, POINTER(c_double)]),
         "lbm_design_gradient": (st, [c_void_p, c_void_p, c_size_t]),
         "lbm_set_design": (st, [c_void_p, c_void_p]),
@@ -130,6 +131,7 @@ def config_from_case(case, precision=LBM_FP32, **overrides) -> LbmConfig:
     for k in range(6):
         c.obj_box[k] = int(case.obj_box[k])
         c.design_box[k] = int(case.design_box[k])
+    c.pipeline = 0
     for k, v in overrides.items():
         setattr(c, k, v)
     return c
@@ -184,6 +186,14 @@ class Solver:
         c, r = c_int32(), c_double()
         check(lib().lbm_window_converged(self.ctx, byref(c), byref(r)), "lbm_window_converged")
         return bool(c.value), r.value
+
+    def window_objectives(self):
+        """Per-slice window means (J, monitor) of a D2Q9 batch."""
+        J = np.empty(self.case.nz, np.float64)
+        M = np.empty(self.case.nz, np.float64)
+        check(lib().lbm_window_objectives(self.ctx, J.ctypes.data, M.ctypes.data, self.case.nz),
+              "lbm_window_objectives")
+        return J, M
 
     def adjoint_window(self):
         j = c_double()

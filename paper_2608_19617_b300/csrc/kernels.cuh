@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
   const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
-  const int z = L::D == 3 ? 1 + int(blockIdx.z) : 0;
+  const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
   R bj = 0, bm = 0;
   if (x < g.nx - 1)
     forward_node<L, R, false>(A, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
@@ -479,8 +479,8 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   const Geo& g = A.geo;
   const unsigned k = blockIdx.x * kBlock + threadIdx.x;
   R bj = 0, bm = 0;
-  if (k < A.ft.n) {
-    const unsigned i = A.ft.idx[k];
+  const unsigned i = k < A.ft.n ? A.ft.idx[k] : kNone;   // rows padded per slice hold kNone
+  if (i != kNone) {
     const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
     forward_node<L, R, true>(A, x, y, z, i, k, bj, bm);
   }
@@ -537,6 +537,41 @@ __global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, in
   acc->mprev = mm;
   acc->has_prev = 1;
   acc->nonfinite = *nonfinite;
+}
+
+// Per-slice window means of a batch of independent 2D lattices (D2Q9, nz > 1):
+// one block per slice sums the block sums of that slice's interior blocks
+// (bz == slice) and face blocks (slice-aligned) in a fixed order.  Runs before
+// window_end_kernel, which clears the block sums.
+__global__ void __launch_bounds__(kEndThreads) slice_end_kernel(const double* blk, int igx, int igy, int fbs,
+                                                                int nint, double nsamples, const double* jconst,
+                                                                double mon_scale, int mon_kind, double* out) {
+  __shared__ double sh[4][kEndThreads];
+  const int slice = blockIdx.x, t = threadIdx.x;
+  const int nib = igx * igy;              // interior blocks of one slice
+  double sj = 0, cj = 0, sm = 0, cm = 0;
+  for (int b = t; b < nib + fbs; b += kEndThreads) {
+    const int bid = b < nib ? slice * nib + b : nint + slice * fbs + (b - nib);
+    const double4 a = reinterpret_cast<const double4*>(blk)[bid];
+    neumaier(sj, cj, a.x);
+    neumaier(sj, cj, a.y);
+    neumaier(sm, cm, a.z);
+    neumaier(sm, cm, a.w);
+  }
+  sh[0][t] = sj; sh[1][t] = cj; sh[2][t] = sm; sh[3][t] = cm;
+  for (int stride = kEndThreads / 2; stride > 0; stride >>= 1) {
+    __syncthreads();
+    if (t < stride) {
+      neumaier(sh[0][t], sh[1][t], sh[0][t + stride]);
+      sh[1][t] += sh[1][t + stride];
+      neumaier(sh[2][t], sh[3][t], sh[2][t + stride]);
+      sh[3][t] += sh[3][t + stride];
+    }
+  }
+  if (t != 0) return;
+  const double jm = (sh[0][0] + sh[1][0]) / nsamples + jconst[slice];
+  out[2 * slice] = jm;
+  out[2 * slice + 1] = mon_kind == MON_DRAG ? (sh[2][0] + sh[3][0]) / nsamples * mon_scale : jm;
 }
 
 // ---------------------------------------------------------------------------
@@ -819,7 +854,7 @@ __global__ void __launch_bounds__(kBlock) adj_interior_kernel(AdjArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
   const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
-  const int z = L::D == 3 ? 1 + int(blockIdx.z) : 0;
+  const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
   if (x >= g.nx - 1) return;
   adjoint_node<L, R, false>(A, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u);
 }
@@ -831,6 +866,7 @@ __global__ void __launch_bounds__(kBlock) adj_face_kernel(AdjArgs<R> A) {
   const unsigned k = blockIdx.x * kBlock + threadIdx.x;
   if (k >= A.ft.n) return;
   const unsigned i = A.ft.idx[k];
+  if (i == kNone) return;
   const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
   adjoint_node<L, R, true>(A, x, y, z, i, k);
 }

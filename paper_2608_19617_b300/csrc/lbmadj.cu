@@ -77,18 +77,20 @@ unsigned mask_with_cx(int sx) {
 // Layout of the caller's workspace.
 struct Layout {
   size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gpart, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
-      partials, acc, flags, f_idx, f_info, f_u0, f_src, f_dst, f_ext, xraw, xfilt, wfilt, total;
+      partials, acc, flags, f_idx, f_info, f_u0, f_src, f_dst, f_ext, xraw, xfilt, wfilt, slice_j, slice_c, total;
   int nblocks_fwd, nblocks_1d, nslots;
   int igx, igy, igz;          // interior grid (blocks of kBlock along x)
+  size_t seg_sets;            // 2 when recompute and adjoint are pipelined
   unsigned nface;             // face nodes
   int face_blocks;
+  int fbs;                    // D2Q9: face blocks per slice (rows padded per slice)
   bool stage_in_seg;
 };
 
 lbm_status validate_config(const lbm_config& c) {
   if (c.lattice != LBM_D2Q9 && c.lattice != LBM_D3Q19) return fail(LBM_ERR_ARG, "lattice must be 9 or 19");
   if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(LBM_ERR_ARG, "lattice sizes must be >= 1");
-  if (c.lattice == LBM_D2Q9 && c.nz != 1) return fail(LBM_ERR_ARG, "D2Q9 needs nz == 1");
+  // D2Q9 with nz > 1 is a batch of nz independent 2D lattices (c_z = 0).
   if (c.ny > 65535 || c.nz > 65535) return fail(LBM_ERR_ARG, "ny and nz must be <= 65535");
   if (double(c.nx) * c.ny * c.nz * c.lattice >= 2147483647.0)
     return fail(LBM_ERR_ARG, "Q * nx * ny * nz must stay below 2^31 (32-bit element indices)");
@@ -115,6 +117,7 @@ lbm_status validate_config(const lbm_config& c) {
   if (c.ckpt_format != LBM_CKPT_NATIVE && c.precision != LBM_FP32)
     return fail(LBM_ERR_ARG, "16-bit checkpoints need the FP32 solver");
   if (!(c.conv_tol >= 0.0)) return fail(LBM_ERR_ARG, "conv_tol must be >= 0");
+  if (c.pipeline != 0 && c.pipeline != 1) return fail(LBM_ERR_ARG, "pipeline must be 0 or 1");
   for (const int32_t* bx : {c.obj_box, c.design_box})
     for (int k = 0; k < 3; ++k)
       if (bx[2 * k] < 0 || bx[2 * k] > bx[2 * k + 1] || bx[2 * k + 1] > dims[k])
@@ -131,11 +134,20 @@ Layout make_layout(const lbm_config& c) {
   const size_t lat = align_up(size_t(q) * n * rs);
   // Interior nodes (off every face) run in one kernel, face nodes in another.
   const int ix = c.nx > 2 ? c.nx - 2 : 0, iy = c.ny > 2 ? c.ny - 2 : 0;
-  const int iz = c.lattice == LBM_D2Q9 ? 1 : (c.nz > 2 ? c.nz - 2 : 0);
+  const bool d2 = c.lattice == LBM_D2Q9;
+  const int iz = d2 ? c.nz : (c.nz > 2 ? c.nz - 2 : 0);
   L.igx = (ix + lbm::kBlock - 1) / lbm::kBlock;
   L.igy = iy;
   L.igz = iz;
-  L.nface = unsigned(n - size_t(ix) * iy * iz);
+  if (d2) {
+    // face rows padded per slice so that every face block belongs to one slice
+    const size_t per = size_t(c.nx) * c.ny - size_t(ix) * iy;
+    L.fbs = int((per + lbm::kBlock - 1) / lbm::kBlock);
+    L.nface = unsigned(size_t(L.fbs) * lbm::kBlock * c.nz);
+  } else {
+    L.nface = unsigned(n - size_t(ix) * iy * iz);
+    L.fbs = 0;
+  }
   L.face_blocks = int((L.nface + lbm::kBlock - 1) / lbm::kBlock);
   L.nblocks_fwd = L.igx * L.igy * L.igz + L.face_blocks;
   L.nblocks_1d = int((n + lbm::kBlock - 1) / lbm::kBlock);
@@ -167,14 +179,17 @@ Layout make_layout(const lbm_config& c) {
   L.f_dst = take(size_t(L.nface) * 4 * q);
   L.f_ext = take(size_t(L.nface) * 4 * q);
   L.xraw = take(n * 4);       // raw design variables (filtered designs)
+  L.slice_j = take(size_t(c.nz) * 16);   // per-slice window means (J, M) of a D2Q9 batch
+  L.slice_c = take(size_t(c.nz) * 8);    // per-slice constant of a pressure objective
   L.xfilt = take(n * 8);      // filtered field x~
   L.wfilt = take(n * 8);      // filter normalisation W_i
   L.acc = take(sizeof(lbm::WindowAcc));
   L.flags = take(16);
   L.ckpt = take(L.ckpt_slot * L.nslots);
-  L.seg = take(lat * L.seg_slots);
+  L.seg_sets = c.pipeline ? 2 : 1;
+  L.seg = take(lat * L.seg_slots * L.seg_sets);
   const size_t stage_bytes = size_t(q) * n * 8;
-  L.stage_in_seg = lat * L.seg_slots >= stage_bytes;
+  L.stage_in_seg = lat * L.seg_slots * L.seg_sets >= stage_bytes;
   L.stage = L.stage_in_seg ? L.seg : take(stage_bytes);
   L.total = off;
   return L;
@@ -219,6 +234,12 @@ struct lbm_ctx {
   cudaStream_t cap = nullptr; // private stream used only to capture graphs
   cudaStream_t side = nullptr;            // face kernels run here, forked from ls and joined back
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  // Pipelined adjoint: the recompute of the next segment runs on rec (with its
+  // own side stream) while the adjoint of the current segment runs on ls.
+  cudaStream_t rec = nullptr, rec_side = nullptr;
+  cudaEvent_t rec_fork = nullptr, rec_join = nullptr, start_ev = nullptr, rec_done[2] = {}, adj_done[2] = {};
+  cudaStream_t side_cur = nullptr;        // side stream / events of the stream now in ls
+  cudaEvent_t fork_cur = nullptr, join_cur = nullptr;
   bool use_graphs = true;
   bool use_pdl = false;
   bool capturing = false;
@@ -249,11 +270,13 @@ struct lbm_ctx {
   void* adjbuf(int k) const { return ws + lay.b[k]; }
   void* seg_slot(int s, int j) const {   // state p^{n0 + sK - 1 + j}
     const size_t lat = align_up(q * n * rs);
+    const size_t set = lay.seg_sets == 2 ? size_t(s & 1) : 0;   // pipelined: segments alternate buffers
+    char* base = ws + lay.seg + set * lat * lay.seg_slots;
     if (cfg.ckpt_format == LBM_CKPT_NATIVE) {
       if (j == 0) return ws + lay.ckpt + lay.ckpt_slot * s;
-      return ws + lay.seg + lat * (j - 1);
+      return base + lat * (j - 1);
     }
-    return ws + lay.seg + lat * j;
+    return base + lat * j;
   }
 
   cudaEvent_t event() {
@@ -321,8 +344,10 @@ struct lbm_ctx {
     for (auto e : pool) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
     if (side) cudaStreamDestroy(side);
-    if (fork_ev) cudaEventDestroy(fork_ev);
-    if (join_ev) cudaEventDestroy(join_ev);
+    if (rec) cudaStreamDestroy(rec);
+    if (rec_side) cudaStreamDestroy(rec_side);
+    for (cudaEvent_t e : {fork_ev, join_ev, rec_fork, rec_join, start_ev, rec_done[0], rec_done[1], adj_done[0], adj_done[1]})
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -371,12 +396,12 @@ struct ImplT final : Impl {
   // parallel branches when captured into a graph).
   template <class IK, class FK>
   void fork_join(IK interior, FK face) {
-    cudaEventRecord(c->fork_ev, c->ls);
-    cudaStreamWaitEvent(c->side, c->fork_ev, 0);
-    face(c->side);
+    cudaEventRecord(c->fork_cur, c->ls);
+    cudaStreamWaitEvent(c->side_cur, c->fork_cur, 0);
+    face(c->side_cur);
     if (has_interior()) interior(c->ls);
-    cudaEventRecord(c->join_ev, c->side);
-    cudaStreamWaitEvent(c->ls, c->join_ev, 0);
+    cudaEventRecord(c->join_cur, c->side_cur);
+    cudaStreamWaitEvent(c->ls, c->join_cur, 0);
   }
   lbm::Phys<R> phys() const { return {R(c->cfg.tau), R(c->cfg.cs_smag * c->cfg.cs_smag), R(c->cfg.rho_out)}; }
   lbm::Obj<R> obj() const {
@@ -573,6 +598,12 @@ lbm_status enqueue_window(lbm_ctx* c) {
   }
   const double mon_scale =
       k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
+  if (k.lattice == LBM_D2Q9) {
+    lbm::slice_end_kernel<<<k.nz, lbm::kEndThreads, 0, c->ls>>>(
+        c->at<double>(c->lay.partials), c->lay.igx, c->lay.igy, c->lay.fbs, c->lay.igx * c->lay.igy * c->lay.igz,
+        double(k.window_len / k.sample_every), c->at<double>(c->lay.slice_c), mon_scale, k.monitor_kind,
+        c->at<double>(c->lay.slice_j));
+  }
   lbm::window_end_kernel<<<1, lbm::kEndThreads, 0, c->ls>>>(
       c->at<double>(c->lay.partials), c->lay.nblocks_fwd, c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol,
       c->at<int>(c->lay.flags), double(k.window_len / k.sample_every), c->jconst, mon_scale, k.monitor_kind);
@@ -581,22 +612,56 @@ lbm_status enqueue_window(lbm_ctx* c) {
 
 // Work of one adjoint sweep (Alg. 2 reverse loop): per segment, restore,
 // recompute K-1 states, then K adjoint steps from the last state back.
+// Pipelined (cfg.pipeline): segment s-1 is restored and recomputed on the
+// rec stream into the other segment buffer while the adjoint of segment s
+// runs on ls; events order each recompute after the adjoint that last used
+// its buffer and each adjoint after its segment's recompute.
 lbm_status enqueue_adjoint(lbm_ctx* c) {
   const lbm_config& k = c->cfg;
   const int K = k.ckpt_every, S = c->lay.nslots;
   const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
+  const bool pipe = c->lay.seg_sets == 2;
   CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gacc), 0, c->n * 16, c->ls));
   CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gpart), 0, c->n * c->rs, c->ls));
-  int bo = 0;
-  const void* bnext = nullptr;
-  for (int s = S - 1; s >= 0; --s) {
+  cudaStream_t main = c->ls;
+  auto on_rec = [&](bool rec) {   // route launches (and their face kernels) to one pipeline stream
+    c->ls = rec ? c->rec : main;
+    c->side_cur = rec ? c->rec_side : c->side;
+    c->fork_cur = rec ? c->rec_fork : c->fork_ev;
+    c->join_cur = rec ? c->rec_join : c->join_ev;
+  };
+  auto recompute = [&](int s) {
     cudaEvent_t e = c->begin();
     if (!native) c->impl->decode(s, c->seg_slot(s, 0));
     c->end(e, 3, native ? 0 : 1, 0);
     e = c->begin();
     for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
     c->end(e, 1, K - 1, int64_t(K - 1) * int64_t(c->n));
-    e = c->begin();
+  };
+  if (pipe) {
+    cudaEventRecord(c->start_ev, main);
+    cudaStreamWaitEvent(c->rec, c->start_ev, 0);
+    on_rec(true);
+    recompute(S - 1);
+    cudaEventRecord(c->rec_done[(S - 1) & 1], c->rec);
+    on_rec(false);
+  }
+  int bo = 0;
+  const void* bnext = nullptr;
+  for (int s = S - 1; s >= 0; --s) {
+    if (!pipe) {
+      recompute(s);
+    } else {
+      if (s >= 1) {
+        on_rec(true);
+        if (s + 1 <= S - 1) cudaStreamWaitEvent(c->rec, c->adj_done[(s + 1) & 1], 0);
+        recompute(s - 1);
+        cudaEventRecord(c->rec_done[(s - 1) & 1], c->rec);
+        on_rec(false);
+      }
+      cudaStreamWaitEvent(main, c->rec_done[s & 1], 0);
+    }
+    cudaEvent_t e = c->begin();
     for (int j = K - 1; j >= 0; --j) {
       const int step = s * K + j;
       c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), step % k.sample_every == 0);
@@ -605,6 +670,7 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
     }
     c->end(e, 2, K, int64_t(K) * int64_t(c->n));
     c->impl->fold();
+    if (pipe) cudaEventRecord(c->adj_done[s & 1], main);
   }
   return LBM_OK;
 }
@@ -642,7 +708,17 @@ lbm_status build_face_table(lbm_ctx* c, const uint8_t* cls, const float* inlet_u
     j = unsigned(p[0]) + unsigned(k.nx) * (unsigned(p[1]) + unsigned(k.ny) * unsigned(p[2]));
     return true;
   };
-  for (int z = 0; z < k.nz; ++z)
+  auto pad_to = [&](size_t rows) {   // empty rows (node kNone) up to a row count
+    while (idx.size() < rows) {
+      const unsigned r = unsigned(idx.size());
+      for (int a = 0; a < L::Q; ++a) src[size_t(a) * nf + r] = dst[size_t(a) * nf + r] = ext[size_t(a) * nf + r] = 0;
+      idx.push_back(lbm::kNone);
+      info.push_back(0);
+      u0.push_back(0.f);
+    }
+  };
+  for (int z = 0; z < k.nz; ++z) {
+    if (!d3) pad_to(size_t(z) * lay.fbs * lbm::kBlock);
     for (int y = 0; y < k.ny; ++y)
       for (int x = 0; x < k.nx; ++x) {
         if (!(x == 0 || x == k.nx - 1 || y == 0 || y == k.ny - 1 || (d3 && (z == 0 || z == k.nz - 1)))) continue;
@@ -674,6 +750,8 @@ lbm_status build_face_table(lbm_ctx* c, const uint8_t* cls, const float* inlet_u
         info.push_back(mask | (unsigned(kind) << 24));
         u0.push_back(kind == LBM_INLET ? uin[size_t(y) + size_t(k.ny) * z] : 0.f);
       }
+  }
+  if (!d3) pad_to(nf);
   if (idx.size() != nf) return fail(LBM_ERR_ARG, "face count mismatch");
   cudaStream_t s = c->stream;
   CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_idx), idx.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
@@ -775,6 +853,16 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
   CUDA_TRY(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
+  ctx->side_cur = ctx->side;
+  ctx->fork_cur = ctx->fork_ev;
+  ctx->join_cur = ctx->join_ev;
+  if (c.pipeline) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->rec, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->rec_side, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&ctx->rec_fork, &ctx->rec_join, &ctx->start_ev, &ctx->rec_done[0], &ctx->rec_done[1],
+                           &ctx->adj_done[0], &ctx->adj_done[1]})
+      CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
   if (c.lattice == LBM_D2Q9) {
     if (c.precision == LBM_FP32) ctx->impl.reset(new ImplT<D2Q9, float>(x));
     else ctx->impl.reset(new ImplT<D2Q9, double>(x));
@@ -815,6 +903,28 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
           sw = t;
         }
     ctx->jconst = (sw + cw) / 3.0;
+  }
+  {
+    // per-slice constants (D2Q9 batches); zero unless the objective is a pressure
+    std::vector<double> sc(size_t(c.nz), 0.0);
+    if (c.objective_kind == LBM_OBJ_PRESSURE && objective_weights) {
+      std::vector<float> w(n);
+      CUDA_TRY(cudaMemcpy(w.data(), objective_weights, n * 4, cudaMemcpyDefault));
+      const int* b = c.obj_box;
+      for (int z = b[4]; z < b[5]; ++z) {
+        double sw = 0, cw = 0;
+        for (int y = b[2]; y < b[3]; ++y)
+          for (int xx = b[0]; xx < b[1]; ++xx) {
+            const double v = w[size_t(xx) + size_t(c.nx) * (size_t(y) + size_t(c.ny) * z)];
+            const double t = sw + v;
+            cw += std::fabs(sw) >= std::fabs(v) ? (sw - t) + v : (v - t) + sw;
+            sw = t;
+          }
+        sc[size_t(z)] = (sw + cw) / 3.0;
+      }
+    }
+    CUDA_TRY(cudaMemcpyAsync(x->at(lay.slice_c), sc.data(), sc.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
   }
   {
     std::vector<float> u(size_t(c.ny) * c.nz, 0.f);
@@ -869,6 +979,21 @@ lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window)
   c->converged = c->nwin_for_ratio >= 2 ? acc.converged : 0;
   if (J_window) *J_window = acc.jmean;
   if (monitor_window) *monitor_window = acc.mmean;
+  return LBM_OK;
+}
+
+lbm_status lbm_window_objectives(lbm_ctx* c, double* J, double* monitor, size_t nslices) {
+  if (!c || !J) return fail(LBM_ERR_ARG, "null argument");
+  if (c->cfg.lattice != LBM_D2Q9) return fail(LBM_ERR_ARG, "per-slice objectives exist for D2Q9 batches only");
+  if (nslices != size_t(c->cfg.nz)) return fail(LBM_ERR_ARG, "nslices %zu, expected nz = %d", nslices, c->cfg.nz);
+  if (!c->window_valid) return fail(LBM_ERR_STATE, "no completed window");
+  std::vector<double> h(2 * nslices);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), c->at(c->lay.slice_j), h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (size_t s = 0; s < nslices; ++s) {
+    J[s] = h[2 * s];
+    if (monitor) monitor[s] = h[2 * s + 1];
+  }
   return LBM_OK;
 }
 

@@ -230,6 +230,20 @@ def small_duct3d(nx=10, ny=6, nz=6, *, tau=0.56, cs_smag=0.1, u_in=0.05,
                 ckpt_every=ckpt_every or window_len, design_box=(1, nx - 1, 1, ny - 1, z0, z1))
 
 
+def stack_cases(cases, name=None) -> Case:
+    """A batch of independent 2D problems: the D2Q9 cases (same size and
+    parameters; designs, weights, inlet profiles and classes may differ) as
+    the z-slices of one lattice.  Boxes become the union over the slices."""
+    c0 = cases[0]
+    assert c0.lattice == 9 and all(c.lattice == 9 and c.nz == 1 and (c.nx, c.ny) == (c0.nx, c0.ny) for c in cases)
+    cat = lambda a: np.concatenate([getattr(c, a) for c in cases], axis=0)
+    b = list(c0.design_box)
+    b[4], b[5] = 0, len(cases)
+    return c0.replace(name=name or f"{c0.name}x{len(cases)}", nz=len(cases), node_class=cat("node_class"),
+                      gamma=cat("gamma"), obj_weights=cat("obj_weights"), inlet_u=cat("inlet_u"),
+                      design_box=tuple(b), periodic=(c0.periodic[0], c0.periodic[1], 0))
+
+
 def periodic_box(nx, ny, nz=1, *, lattice=9, tau=0.6, cs_smag=0.0, gamma=None):
     """Fully periodic domain (no boundary nodes); used for invariance tests."""
     cls = np.zeros((nz, ny, nx), np.uint8)

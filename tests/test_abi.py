@@ -66,7 +66,7 @@ def _cfg(**kw):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("tau", 0.5), ("lattice", 7), ("nz", 2), ("window_len", 0), ("sample_every", 3),
+    ("tau", 0.5), ("lattice", 7), ("nz", 0), ("window_len", 0), ("sample_every", 3),
     ("ckpt_every", 7), ("g_max", 1.5), ("precision", 5), ("rho_out", -1.0),
     ("objective_kind", 9), ("q_interp", 0.0), ("ckpt_format", 3),
 ])
@@ -77,6 +77,13 @@ def test_invalid_configs_are_rejected(lib, field, value):
         B.workspace_size(cfg)
     assert e.value.status == B.LBM_ERR_ARG
     assert B.last_error()
+
+
+def test_d2q9_batches_are_valid_configs(lib):
+    """nz > 1 with D2Q9 stacks independent 2D lattices (a batch)."""
+    cfg = _cfg()
+    cfg.nz = 5
+    assert B.workspace_size(cfg) > B.workspace_size(_cfg())
 
 
 def test_sixteen_bit_checkpoints_need_fp32(lib):

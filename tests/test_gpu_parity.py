@@ -373,3 +373,138 @@ def test_filtered_design_and_its_gradient_match_oracle():
     dgamma = np.where(m.reshape(-1), dgamma, 0.0)          # the library's gradient is zero off the box
     want = O.filter_project_adjoint(x_raw.astype(np.float64), dgamma, shape, case.design_box, radius, beta, eta)
     assert rel_err(g_raw, want) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["diss-zouhe", "d3q19-pressure"])
+def test_adjoint_matches_central_differences_on_the_gpu(name):
+    """Single-node protocol of Sec. 4.2.1 run entirely on the GPU (FP64 path):
+    central differences of the window objective (steps 2e-3 and 1e-3 on one
+    FP32 design value, Richardson-extrapolated), same window and sampling
+    instants, against the adjoint gradient."""
+    case = f32_inputs(ADJ_CASES[name]())
+    pr = O.Problem(case)
+    p0 = _developed(pr, 40)
+    sol = B.Solver(case, B.LBM_FP64)
+    sol.set_state(p0)
+    sol.step_window()
+    sol.adjoint_window()
+    grad = sol.design_gradient()
+    gam = case.gamma.reshape(-1).astype(np.float32)
+    x0, x1, y0, y1, z0, z1 = case.design_box
+    rng = np.random.default_rng(4)
+    nodes = []
+    while len(nodes) < 4:
+        x, y, z = rng.integers(x0, x1), rng.integers(y0, y1), rng.integers(z0, z1)
+        i = int(x + case.nx * (y + case.ny * z))
+        if 2e-3 < gam[i] < 1 - 2e-3 and abs(grad[i]) > 1e-3 * np.abs(grad).max():
+            nodes.append(i)
+    def central(i, step):
+        js, vals = [], []
+        for sgn in (1, -1):
+            g2 = gam.copy()
+            g2[i] += np.float32(sgn * step)
+            vals.append(float(g2[i]))                 # the FP32 value actually set
+            sol.set_design(g2)
+            sol.set_state(p0)
+            js.append(sol.step_window()[0])
+        h = 0.5 * (vals[0] - vals[1])
+        return (js[0] - js[1]) / (2 * h), h
+
+    for i in nodes:
+        # Richardson extrapolation of two central differences removes the h^2 term
+        (d1, h1), (d2, h2) = central(i, 2e-3), central(i, 1e-3)
+        fd = (h1 * h1 * d2 - h2 * h2 * d1) / (h1 * h1 - h2 * h2)
+        assert abs(fd - grad[i]) <= 1e-6 * abs(grad[i]), (i, fd, grad[i])
+
+
+@pytest.mark.parametrize("fmt", [I.CKPT_NATIVE, I.CKPT_BF16])
+def test_pipelined_adjoint_matches_serial(fmt):
+    """Recomputing segment s-1 while the adjoint sweeps segment s (two segment
+    buffers, two streams) gives bitwise the serial results, with and without
+    graph replay."""
+    case = f32_inputs(I.small_channel(150, 12, window_len=24, ckpt_every=4, ckpt_format=fmt,
+                                      outlet=I.OUTLET_P, tau=0.53))
+    pr = O.Problem(case)
+    p0 = _developed(pr, 20)
+    out = []
+    for pipeline, graphs in ((0, True), (1, True), (1, False)):
+        sol = B.Solver(case, B.LBM_FP32, pipeline=pipeline)
+        sol.set_graphs(graphs)
+        sol.set_state(p0)
+        for _ in range(2):
+            sol.step_window()
+            sol.adjoint_window()
+        out.append((sol.design_gradient(), sol.get_adjoint_state()))
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+
+
+def test_batch_of_replicas_matches_single_runs():
+    """A D2Q9 batch (independent 2D problems as z-slices, one launch per step)
+    gives each slice's window mean and gradient as a run of that problem alone
+    would (FP64), and the batch matches the oracle."""
+    cases = [f32_inputs(I.small_channel(140, 11, window_len=10, seed=s, outlet=I.OUTLET_P, tau=0.53,
+                                        u_in=0.04 + 0.005 * s, obj_kind=k))
+             for s, k in ((1, I.OBJ_DISSIPATION), (2, I.OBJ_DISSIPATION), (3, I.OBJ_DISSIPATION))]
+    batch = I.stack_cases(cases)
+    p0s = [_developed(O.Problem(c), 20) for c in cases]
+    sol = B.Solver(batch, B.LBM_FP64)
+    sol.set_state(np.concatenate(p0s, axis=1))
+    Jtot, _ = sol.step_window()
+    Js, _ = sol.window_objectives()
+    sol.adjoint_window()
+    gb = sol.design_gradient().reshape(len(cases), -1)
+    assert abs(Js.sum() - Jtot) <= 1e-12 * abs(Jtot)
+    for s, (c, p0) in enumerate(zip(cases, p0s)):
+        one = B.Solver(c, B.LBM_FP64)
+        one.set_state(p0)
+        J1, _ = one.step_window()
+        one.adjoint_window()
+        g1 = one.design_gradient()
+        assert abs(Js[s] - J1) <= 1e-12 * abs(J1)
+        assert rel_err(gb[s], g1) < 1e-12
+    pr = O.Problem(batch)
+    _, Jw, _, traj = pr.run_window(np.concatenate(p0s, axis=1))
+    _, gw, _ = pr.adjoint_window(traj)
+    assert abs(Jtot - Jw) <= 1e-12 * abs(Jw)
+    x0, x1, y0, y1, z0, z1 = batch.design_box
+    m = np.zeros((batch.nz, batch.ny, batch.nx), bool)
+    m[z0:z1, y0:y1, x0:x1] = True
+    assert rel_err(gb.reshape(-1)[m.reshape(-1)], gw[m.reshape(-1)]) < 1e-11
+
+
+def test_finite_difference_protocol_as_one_batch():
+    """The single-node protocol of Sec. 4.2.1 as one batched run: slice 0 is
+    the base design, the others carry +-h perturbations of selected nodes; the
+    per-slice window means give central differences (Richardson over two
+    steps) that match the base slice's adjoint gradient."""
+    base = f32_inputs(I.small_channel(140, 11, window_len=10, outlet=I.OUTLET_P, tau=0.53))
+    p0 = _developed(O.Problem(base), 30)
+    gam = base.gamma.astype(np.float32)
+    nodes = [(5, 30), (6, 70), (4, 100)]
+    steps = (2e-3, 1e-3)
+    cases, vals = [base], []
+    for (y, x) in nodes:
+        for h in steps:
+            for sgn in (1, -1):
+                g2 = gam.copy()
+                g2[0, y, x] += np.float32(sgn * h)
+                vals.append(float(g2[0, y, x]))
+                cases.append(base.replace(gamma=g2.astype(np.float64)))
+    batch = I.stack_cases(cases)
+    sol = B.Solver(batch, B.LBM_FP64)
+    sol.set_state(np.concatenate([p0] * len(cases), axis=1))
+    sol.step_window()
+    Js, _ = sol.window_objectives()
+    sol.adjoint_window()
+    grad0 = sol.design_gradient().reshape(len(cases), base.ny, base.nx)[0]
+    k = 1
+    for n, (y, x) in enumerate(nodes):
+        d = []
+        for h in steps:
+            vp, vm = vals[k - 1], vals[k]
+            d.append(((Js[k] - Js[k + 1]) / (vp - vm), 0.5 * (vp - vm)))
+            k += 2
+        (d1, h1), (d2, h2) = d
+        fd = (h1 * h1 * d2 - h2 * h2 * d1) / (h1 * h1 - h2 * h2)
+        assert abs(fd - grad0[y, x]) <= 1e-6 * abs(grad0[y, x]), (y, x, fd, grad0[y, x])

@@ -233,6 +233,41 @@ lbm_status lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
  * Results are identical either way. */
 lbm_status lbm_set_pdl(lbm_ctx* ctx, int32_t enable);
 
+/* Run each checkpoint segment of the forward window, of the recompute and of
+ * the adjoint sweep as ONE persistent launch (1) instead of one launch per
+ * step (0, the default).  The persistent kernels (a library design with no
+ * counterpart in the paper) cut the lattice into bands of consecutive nodes,
+ * one block per band, all blocks co-resident (cooperative launch); a block
+ * starts step k once the bands its step reads from or writes over have
+ * finished step k-1.  Nodes are computed by the same arithmetic as in the
+ * per-step kernels (compiled in another context: results agree to a few
+ * units in the last place); window sums are added in another order.
+ * The adjoint sweep then runs serially (cfg.pipeline is ignored).  Every wait
+ * is bounded (4 s without progress): a wait that runs out makes the window or
+ * sweep fail with LBM_ERR_CUDA instead of hanging.  Fails with LBM_ERR_ARG
+ * where the schedule does not exist: D2Q9 batches (nz > 1) or a device
+ * without cooperative launch. */
+lbm_status lbm_set_flow(lbm_ctx* ctx, int32_t enable);
+
+/* Test hook of the persistent kernels' bounded waits: the longest wait without
+ * progress (seconds, default 4) and one band that computes but never
+ * publishes its progress (-1, the default: none), so that its neighbours'
+ * waits run out and the window or sweep fails with LBM_ERR_CUDA while the
+ * context stays usable.  Not for production use. */
+lbm_status lbm_set_flow_test_hook(lbm_ctx* ctx, double wait_seconds, int32_t silent_band);
+
+/* How the context launches its work. */
+typedef struct {
+  int32_t flow_bands;       /* bands of the persistent schedule (0: unavailable)       */
+  int32_t flow;             /* 1: persistent segment launches (lbm_set_flow)          */
+  int32_t graphs;           /* 1: windows and sweeps replay as CUDA graphs            */
+  int32_t pdl;              /* 1: programmatic dependent launch                       */
+  int64_t kernels_window;   /* kernels enqueued by the last window (0 before one)     */
+  int64_t kernels_adjoint;  /* kernels enqueued by the last adjoint sweep             */
+} lbm_schedule;
+
+lbm_status lbm_get_schedule(lbm_ctx* ctx, lbm_schedule* out);
+
 /* Total steps advanced and windows completed since lbm_create. */
 lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);
 

@@ -46,6 +46,11 @@ class LbmFilter(ctypes.Structure):
     _fields_ = [("radius", c_double), ("beta", c_double), ("eta", c_double)]
 
 
+class LbmSchedule(ctypes.Structure):
+    _fields_ = [("flow_bands", c_int32), ("flow", c_int32), ("graphs", c_int32), ("pdl", c_int32),
+                ("kernels_window", c_int64), ("kernels_adjoint", c_int64)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, func, msg):
         super().__init__(f"{func}: {status_string(status)} ({msg})")
@@ -86,6 +91,9 @@ def lib() -> ctypes.CDLL:
         "lbm_get_counters": (st, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
         "lbm_set_graphs": (st, [c_void_p, c_int32]),
         "lbm_set_pdl": (st, [c_void_p, c_int32]),
+        "lbm_set_flow": (st, [c_void_p, c_int32]),
+        "lbm_get_schedule": (st, [c_void_p, POINTER(LbmSchedule)]),
+        "lbm_set_flow_test_hook": (st, [c_void_p, c_double, c_int32]),
         "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_status_string": (ctypes.c_char_p, [c_int32]),
@@ -266,6 +274,21 @@ class Solver:
 
     def set_pdl(self, enable: bool):
         check(lib().lbm_set_pdl(self.ctx, int(bool(enable))), "lbm_set_pdl")
+
+    def set_flow(self, enable: bool):
+        """Persistent segment launches (lbm_set_flow)."""
+        check(lib().lbm_set_flow(self.ctx, int(bool(enable))), "lbm_set_flow")
+
+    def set_flow_test_hook(self, wait_seconds: float = 4.0, silent_band: int = -1):
+        """Bounded-wait test hook of the persistent kernels (lbm_set_flow_test_hook)."""
+        check(lib().lbm_set_flow_test_hook(self.ctx, float(wait_seconds), int(silent_band)),
+              "lbm_set_flow_test_hook")
+
+    def schedule(self) -> dict:
+        """Launch configuration and kernels per window / adjoint sweep (lbm_get_schedule)."""
+        out = LbmSchedule()
+        check(lib().lbm_get_schedule(self.ctx, byref(out)), "lbm_get_schedule")
+        return {f: getattr(out, f) for f, _ in LbmSchedule._fields_}
 
     def counters(self):
         s, w = c_int64(), c_int64()

@@ -72,7 +72,8 @@ struct Obj {
 // Window-end results.
 struct WindowAcc {
   double jmean, mmean, mprev, ratio;
-  int has_prev, converged, nonfinite, pad;
+  int has_prev, converged, nonfinite;
+  int stalled;   // a persistent step kernel gave up waiting (flags[2])
 };
 
 template <class T>
@@ -351,9 +352,9 @@ __device__ __forceinline__ void post_collision(const Mom<L, R>& M, R g, R& A, R 
 // ---------------------------------------------------------------------------
 // Block reduction of two values in the working precision; result in thread 0.
 // ---------------------------------------------------------------------------
-template <class R>
+template <class R, int NT = kBlock>
 __device__ __forceinline__ void block_sum2(R& a, R& b) {
-  __shared__ R sa[kBlock / 32], sb[kBlock / 32];
+  __shared__ R sa[NT / 32], sb[NT / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
@@ -366,7 +367,7 @@ __device__ __forceinline__ void block_sum2(R& a, R& b) {
     a = sa[0];
     b = sb[0];
 #pragma unroll
-    for (int k = 1; k < kBlock / 32; ++k) { a += sa[k]; b += sb[k]; }
+    for (int k = 1; k < NT / 32; ++k) { a += sa[k]; b += sb[k]; }
   }
 }
 
@@ -419,22 +420,42 @@ __device__ __forceinline__ R local_objective(const Mom<L, R>& M, const Obj<R>& o
   }
 }
 
-// One node of a forward step (interior or face node).
+// Load of a field that other blocks of the same launch write (persistent step
+// kernels): through L2, never from a possibly stale L1 or read-only cache line.
+template <bool CG, class R>
+__device__ __forceinline__ R ldf(const R* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// The per-step fields of a step (persistent kernels change them every step).
+template <class R>
+struct FwdStep {
+  const R* src;   // p^{n-1}
+  R* dst;         // p^n
+  int sample;
+};
+
+// One node of a forward step (interior or face node); a sampled step adds the
+// node's objective and monitor terms to bj, bm.
 // For a face node k is its row in the face table; for an interior node k is unused.
-template <class L, class R, bool FACE>
-__device__ __forceinline__ void forward_node(const FwdArgs<R>& A, int x, int y, int z, unsigned i, unsigned k,
-                                             R& bj, R& bm) {
+// CG: the source field is written concurrently by other blocks of the launch.
+template <class L, class R, bool FACE, bool CG = false>
+__device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<R>& P, int x, int y, int z,
+                                             unsigned i, unsigned k, R& bj, R& bm) {
   const Geo& g = A.geo;
+  const R* src = P.src;
+  R* dst = P.dst;
   R f[L::Q];
   if (FACE) {
     const FaceTable& t = A.ft;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = A.src[a * g.n + t.src[a * t.n + k]];
+    for (int a = 0; a < L::Q; ++a) f[a] = ldf<CG>(src + (a * g.n + t.src[a * t.n + k]));
     const unsigned info = t.info[k];
     apply_rules<L, R>(f, info & 0xffffffu, uint8_t(info >> 24), R(t.u0[k]), A.ph.rho_out);
   } else {
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = A.src[a * g.n + i - offset<L>(g, a)];
+    for (int a = 0; a < L::Q; ++a) f[a] = ldf<CG>(src + (a * g.n + i - offset<L>(g, a)));
   }
   Mom<L, R> M;
   moments<L, R>(f, A.ph, M);
@@ -443,14 +464,14 @@ __device__ __forceinline__ void forward_node(const FwdArgs<R>& A, int x, int y, 
   R a0, B[3], T[6];
   post_collision<L, R>(M, gi, a0, B, T);
 #pragma unroll
-  for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
-  if (A.sample) {
+  for (int a = 0; a < L::Q; ++a) dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
+  if (P.sample) {
     const int* b = A.obj.box;
     if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
       const R w = R(A.wobj[i]);
-      if (w != R(0)) bj = w * local_objective<L, R>(M, A.obj, gi);
+      if (w != R(0)) bj += w * local_objective<L, R>(M, A.obj, gi);
     }
-    if (A.obj.mon == MON_DRAG) bm = R(-2) * gi * M.m[0];
+    if (A.obj.mon == MON_DRAG) bm += R(-2) * gi * M.m[0];
   }
 }
 
@@ -464,11 +485,10 @@ __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
   const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
   R bj = 0, bm = 0;
   if (x < g.nx - 1)
-    forward_node<L, R, false>(A, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
+    forward_node<L, R, false>(A, FwdStep<R>{A.src, A.dst, A.sample}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
   if (A.sample) {   // uniform across the grid
     block_sum2<R>(bj, bm);
-    sample_commit(double(bj), double(bm), A.blk,
-                  blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+    sample_commit(double(bj), double(bm), A.blk);
   }
 }
 
@@ -482,7 +502,7 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   const unsigned i = k < A.ft.n ? A.ft.idx[k] : kNone;   // rows padded per slice hold kNone
   if (i != kNone) {
     const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
-    forward_node<L, R, true>(A, x, y, z, i, k, bj, bm);
+    forward_node<L, R, true>(A, FwdStep<R>{A.src, A.dst, A.sample}, x, y, z, i, k, bj, bm);
   }
   if (A.sample) {
     block_sum2<R>(bj, bm);
@@ -536,22 +556,26 @@ __global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, in
   acc->mmean = mm;
   acc->mprev = mm;
   acc->has_prev = 1;
-  acc->nonfinite = *nonfinite;
+  acc->nonfinite = nonfinite[0];
+  acc->stalled = nonfinite[2];
 }
 
 // Per-slice window means of a batch of independent 2D lattices (D2Q9, nz > 1):
 // one block per slice sums the block sums of that slice's interior blocks
-// (bz == slice) and face blocks (slice-aligned) in a fixed order.  Runs before
-// window_end_kernel, which clears the block sums.
+// (bz == slice) and face blocks (slice-aligned) in a fixed order.  With
+// nflat > 0 (a single lattice, nz == 1) the one slice sums blk[0 .. nflat).
+// Runs before window_end_kernel, which clears the block sums.
 __global__ void __launch_bounds__(kEndThreads) slice_end_kernel(const double* blk, int igx, int igy, int fbs,
                                                                 int nint, double nsamples, const double* jconst,
-                                                                double mon_scale, int mon_kind, double* out) {
+                                                                double mon_scale, int mon_kind, double* out,
+                                                                int nflat) {
   __shared__ double sh[4][kEndThreads];
   const int slice = blockIdx.x, t = threadIdx.x;
   const int nib = igx * igy;              // interior blocks of one slice
+  const int count = nflat > 0 ? nflat : nib + fbs;
   double sj = 0, cj = 0, sm = 0, cm = 0;
-  for (int b = t; b < nib + fbs; b += kEndThreads) {
-    const int bid = b < nib ? slice * nib + b : nint + slice * fbs + (b - nib);
+  for (int b = t; b < count; b += kEndThreads) {
+    const int bid = nflat > 0 ? b : b < nib ? slice * nib + b : nint + slice * fbs + (b - nib);
     const double4 a = reinterpret_cast<const double4*>(blk)[bid];
     neumaier(sj, cj, a.x);
     neumaier(sj, cj, a.y);
@@ -701,11 +725,25 @@ __global__ void __launch_bounds__(kBlock) adj_pull_kernel(const R* __restrict__ 
   for (int k = 0; k < L::Q; ++k) out[k * g.n + i] = a[k];
 }
 
+template <class R>
+struct AdjStep {
+  const R* bnext;   // b^{n+1}
+  const R* pprev;   // p^{n-1}
+  R* bout;          // b^n
+  int sample;
+  int terminal;
+};
+
 // One node of an adjoint step (interior or face node).
-template <class L, class R, bool FACE>
-__device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, int x, int y, int z, unsigned i, unsigned kf) {
+// CG: the downstream adjoint field is written concurrently by other blocks.
+template <class L, class R, bool FACE, bool CG = false>
+__device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<R>& P, int x, int y, int z, unsigned i,
+                                             unsigned kf) {
   const Geo& g = A.geo;
   const FaceTable& ft = A.ft;
+  const R* bnext = P.bnext;
+  const R* pprev = P.pprev;
+  R* bout = P.bout;
   const unsigned info = FACE ? ft.info[kf] : 0u;
   const uint8_t cls = uint8_t(info >> 24);
   const unsigned mask = info & 0xffffffu;
@@ -716,19 +754,19 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, int x, int y, 
   R A0, A1[3], A2[6];
   {
     R a[L::Q];
-    if (A.terminal) {
+    if (P.terminal) {
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) a[k] = R(0);
     } else if (FACE) {
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) {
         const unsigned d = ft.dst[k * ft.n + kf], e = ft.ext[k * ft.n + kf];
-        a[k] = d != kNone ? A.bnext[k * g.n + d] : R(0);
-        if (e != kNone) a[k] += A.bnext[k * g.n + e];
+        a[k] = d != kNone ? ldf<CG>(bnext + (k * g.n + d)) : R(0);
+        if (e != kNone) a[k] += ldf<CG>(bnext + (k * g.n + e));
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < L::Q; ++k) a[k] = A.bnext[k * g.n + i + offset<L>(g, k)];
+      for (int k = 0; k < L::Q; ++k) a[k] = ldf<CG>(bnext + (k * g.n + i + offset<L>(g, k)));
     }
     raw_moments<L, R, true>(a, A0, A1, A2);
   }
@@ -736,11 +774,11 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, int x, int y, 
   R f[L::Q];
   if (FACE) {
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = A.pprev[a * g.n + ft.src[a * ft.n + kf]];
+    for (int a = 0; a < L::Q; ++a) f[a] = pprev[a * g.n + ft.src[a * ft.n + kf]];
     apply_rules<L, R>(f, mask, cls, u0, A.ph.rho_out);
   } else {
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = A.pprev[a * g.n + i - offset<L>(g, a)];
+    for (int a = 0; a < L::Q; ++a) f[a] = pprev[a * g.n + i - offset<L>(g, a)];
   }
   Mom<L, R> M;
   moments<L, R>(f, A.ph, M);
@@ -779,7 +817,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, int x, int y, 
 #pragma unroll
   for (int k = 0; k < 6; ++k) cpi[k] = M.om * R(4.5) * Rm[k];
 
-  if (A.sample) {
+  if (P.sample) {
     const int* bx = A.obj.box;
     if (x >= bx[0] && x < bx[1] && y >= bx[2] && y < bx[3] && z >= bx[4] && z < bx[5]) {
       const R ws = R(A.wobj[i]) * A.obj.ws;
@@ -843,7 +881,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, int x, int y, 
   for (int k = 0; k < L::Q; ++k) b[k] = quad_form<L, R>(k, grho, gm, cpi);
   if (FACE) bc_transpose<L, R>(b, mask, cls, u0);
 #pragma unroll
-  for (int k = 0; k < L::Q; ++k) A.bout[k * g.n + i] = b[k];
+  for (int k = 0; k < L::Q; ++k) bout[k * g.n + i] = b[k];
 
   const int* d = A.dbox;
   if (x >= d[0] && x < d[1] && y >= d[2] && y < d[3] && z >= d[4] && z < d[5]) A.gpart[i] += gt;
@@ -856,7 +894,7 @@ __global__ void __launch_bounds__(kBlock) adj_interior_kernel(AdjArgs<R> A) {
   const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
   const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
   if (x >= g.nx - 1) return;
-  adjoint_node<L, R, false>(A, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u);
+  adjoint_node<L, R, false>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u);
 }
 
 template <class L, class R>
@@ -868,7 +906,7 @@ __global__ void __launch_bounds__(kBlock) adj_face_kernel(AdjArgs<R> A) {
   const unsigned i = A.ft.idx[k];
   if (i == kNone) return;
   const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
-  adjoint_node<L, R, true>(A, x, y, z, i, k);
+  adjoint_node<L, R, true>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z, i, k);
 }
 
 // Fold a segment's sensitivity partials into the FP64 (sum, compensation)

@@ -11,6 +11,7 @@
 // per-node FP64 (sum, compensation) pair.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -21,6 +22,7 @@
 
 #include "lbmadj.h"
 #include "filter.cuh"
+#include "flow.cuh"
 #include "kernels.cuh"
 
 namespace {
@@ -77,8 +79,10 @@ unsigned mask_with_cx(int sx) {
 // Layout of the caller's workspace.
 struct Layout {
   size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gpart, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
-      partials, acc, flags, f_idx, f_info, f_u0, f_src, f_dst, f_ext, xraw, xfilt, wfilt, slice_j, slice_c, total;
+      partials, acc, flags, f_idx, f_info, f_u0, f_src, f_dst, f_ext, xraw, xfilt, wfilt, slice_j, slice_c,
+      fl_band, fl_fband, fl_wptr, fl_widx, fl_done, total;
   int nblocks_fwd, nblocks_1d, nslots;
+  int nblocks_sum;            // block-sum slots: per-step kernels' blocks or persistent bands
   int igx, igy, igz;          // interior grid (blocks of kBlock along x)
   size_t seg_sets;            // 2 when recompute and adjoint are pipelined
   unsigned nface;             // face nodes
@@ -171,7 +175,14 @@ Layout make_layout(const lbm_config& c) {
   L.gacc = take(n * 16);
   L.gpart = take(n * rs);
   L.gout = take(n * 8);
-  L.partials = take(size_t(L.nblocks_fwd) * 32);
+  L.nblocks_sum = L.nblocks_fwd > lbm::kFlowMaxBands ? L.nblocks_fwd : lbm::kFlowMaxBands;
+  L.partials = take(size_t(L.nblocks_sum) * 32);
+  // persistent-step schedule: band bounds, face-row bounds, wait sets, progress
+  L.fl_band = take(size_t(lbm::kFlowMaxBands + 1) * 4);
+  L.fl_fband = take(size_t(lbm::kFlowMaxBands + 1) * 4);
+  L.fl_wptr = take(size_t(lbm::kFlowMaxBands + 1) * 4);
+  L.fl_widx = take(size_t(lbm::kFlowMaxBands) * lbm::kFlowMaxWait * 4);
+  L.fl_done = take(size_t(lbm::kFlowMaxBands) * 4);
   L.f_idx = take(size_t(L.nface) * 4);
   L.f_info = take(size_t(L.nface) * 4);
   L.f_u0 = take(size_t(L.nface) * 4);
@@ -217,6 +228,11 @@ struct Impl {
   virtual void to_double(const void* src) = 0;
   virtual void encode(const void* p, int slot) = 0;
   virtual void decode(int slot, void* p) = 0;
+  // Persistent step kernels (see flow.cuh).
+  virtual int flow_capacity() = 0;   // co-resident blocks of the persistent kernels, 0 if none
+  virtual void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every) = 0;
+  virtual void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
+                       int nsteps, int step0) = 0;
 };
 
 // A captured CUDA graph with the timing events its replays record.
@@ -242,6 +258,12 @@ struct lbm_ctx {
   cudaEvent_t fork_cur = nullptr, join_cur = nullptr;
   bool use_graphs = true;
   bool use_pdl = false;
+  int flow_bands = 0;         // bands of the persistent schedule (0: not available)
+  bool use_flow = false;      // run segments as persistent launches
+  unsigned long long flow_wait_ns = 4000000000ull;   // 4 s without progress of a neighbouring band
+  int flow_silent = -1;       // test hook: a band that never publishes
+  int64_t kernels = 0;        // kernel launches enqueued so far
+  int64_t kernels_window = 0, kernels_adjoint = 0;   // per window / per adjoint sweep, as last enqueued
   bool capturing = false;
   std::vector<Pending>* sink = nullptr;   // where end() files events while capturing
   GraphRec gwin[2][2];        // forward window graphs by [start parity][timing]
@@ -399,7 +421,11 @@ struct ImplT final : Impl {
     cudaEventRecord(c->fork_cur, c->ls);
     cudaStreamWaitEvent(c->side_cur, c->fork_cur, 0);
     face(c->side_cur);
-    if (has_interior()) interior(c->ls);
+    c->kernels += 1;
+    if (has_interior()) {
+      interior(c->ls);
+      c->kernels += 1;
+    }
     cudaEventRecord(c->join_cur, c->side_cur);
     cudaStreamWaitEvent(c->ls, c->join_cur, 0);
   }
@@ -415,7 +441,7 @@ struct ImplT final : Impl {
     return o;
   }
 
-  void fwd(const void* src, void* dst, int sample) override {
+  lbm::FwdArgs<R> fwd_args(const void* src, void* dst, int sample) const {
     lbm::FwdArgs<R> A;
     A.src = static_cast<const R*>(src);
     A.dst = static_cast<R*>(dst);
@@ -430,11 +456,9 @@ struct ImplT final : Impl {
     A.blk = c->template at<double>(c->lay.partials);
     A.nonfinite = c->template at<int>(c->lay.flags);
     A.ft = table();
-    const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
-    fork_join([&](cudaStream_t st) { launch(lbm::fwd_interior_kernel<L, R>, igrid(), st, A); },
-              [&](cudaStream_t st) { launch(lbm::fwd_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A, blk0); });
+    return A;
   }
-  void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
+  lbm::AdjArgs<R> adj_args(const void* bnext, const void* pprev, void* bout, int sample) const {
     lbm::AdjArgs<R> A;
     A.bnext = static_cast<const R*>(bnext);
     A.pprev = static_cast<const R*>(pprev);
@@ -451,8 +475,76 @@ struct ImplT final : Impl {
     A.terminal = bnext == nullptr;
     for (int i = 0; i < 6; ++i) A.dbox[i] = c->cfg.design_box[i];
     A.ft = table();
+    return A;
+  }
+  void fwd(const void* src, void* dst, int sample) override {
+    const lbm::FwdArgs<R> A = fwd_args(src, dst, sample);
+    const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
+    fork_join([&](cudaStream_t st) { launch(lbm::fwd_interior_kernel<L, R>, igrid(), st, A); },
+              [&](cudaStream_t st) { launch(lbm::fwd_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A, blk0); });
+  }
+  void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
+    const lbm::AdjArgs<R> A = adj_args(bnext, pprev, bout, sample);
     fork_join([&](cudaStream_t st) { launch(lbm::adj_interior_kernel<L, R>, igrid(), st, A); },
               [&](cudaStream_t st) { launch(lbm::adj_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A); });
+  }
+
+  // Persistent step kernels.
+  int flow_capacity() override {
+    int dev = 0, sms = 0, coop = 0, bf = 0, ba = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, lbm::fwd_flow_kernel<L, R>, lbm::kFlowBlock, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, lbm::adj_flow_kernel<L, R>, lbm::kFlowBlock, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    if (!coop) return 0;
+    return sms * (bf < ba ? bf : ba);
+  }
+  lbm::Flow flow() const {
+    lbm::Flow f;
+    f.band = c->template at<unsigned>(c->lay.fl_band);
+    f.fband = c->template at<unsigned>(c->lay.fl_fband);
+    f.wptr = c->template at<int>(c->lay.fl_wptr);
+    f.widx = c->template at<int>(c->lay.fl_widx);
+    f.done = c->template at<int>(c->lay.fl_done);
+    f.status = c->template at<int>(c->lay.flags) + 2;
+    f.blk = c->template at<double>(c->lay.partials);
+    f.wait_ns = c->flow_wait_ns;
+    f.silent = c->flow_silent;
+    return f;
+  }
+  // Cooperative launch of P bands (all blocks co-resident) after clearing
+  // the progress counters.
+  template <class... Args>
+  void launch_flow(void (*kernel)(Args...), Args... args) {
+    cudaMemsetAsync(c->template at<int>(c->lay.fl_done), 0, size_t(c->flow_bands) * 4, c->ls);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->flow_bands);
+    cfg.blockDim = dim3(lbm::kFlowBlock);
+    cfg.stream = c->ls;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+    c->kernels += 1;
+  }
+  void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every) override {
+    const lbm::FwdArgs<R> A = fwd_args(nullptr, nullptr, 0);
+    const lbm::Chain<R> ch{static_cast<R*>(a), static_cast<R*>(b), (long long)(stride_bytes / sizeof(R))};
+    launch_flow(lbm::fwd_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, sample_every);
+  }
+  void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
+               int nsteps, int step0) override {
+    const lbm::AdjArgs<R> A = adj_args(nullptr, nullptr, nullptr, 0);
+    const lbm::AdjChain<R> ch{static_cast<const R*>(p0), static_cast<const R*>(p1),
+                              (long long)(stride_bytes / sizeof(R)), static_cast<const R*>(bnext0),
+                              static_cast<R*>(o0), static_cast<R*>(o1)};
+    launch_flow(lbm::adj_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, c->cfg.sample_every);
   }
   void pull(const void* b, void* out) override {
     lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(
@@ -467,6 +559,7 @@ struct ImplT final : Impl {
     const long long cells = (long long)(d[1] - d[0]) * (d[3] - d[2]) * (d[5] - d[4]);
     if (cells == 0) return;
     const long long blocks = (cells + 255) / 256;
+    c->kernels += 1;
     lbm::grad_fold_kernel<R><<<int(blocks < 148 * 32 ? blocks : 148 * 32), 256, 0, c->ls>>>(
         c->template at<R>(c->lay.gpart), c->template at<double2>(c->lay.gacc), c->geo, d[0], d[1], d[2], d[3],
         d[4], d[5]);
@@ -497,6 +590,7 @@ struct ImplT final : Impl {
     T* dev = reinterpret_cast<T*>(base);
     float* mom = reinterpret_cast<float*>(base + align_up(c->q * c->n * 2));
     int* ex = reinterpret_cast<int*>(base + align_up(c->q * c->n * 2) + align_up((L::D + 1) * c->n * 4));
+    c->kernels += 1;
     lbm::ckpt_encode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->ls>>>(
         static_cast<const float*>(p), dev, mom, ex, (long long)c->n);
   }
@@ -506,6 +600,7 @@ struct ImplT final : Impl {
     T* dev = reinterpret_cast<T*>(base);
     float* mom = reinterpret_cast<float*>(base + align_up(c->q * c->n * 2));
     int* ex = reinterpret_cast<int*>(base + align_up(c->q * c->n * 2) + align_up((L::D + 1) * c->n * 4));
+    c->kernels += 1;
     lbm::ckpt_decode_kernel<L, T><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->ls>>>(
         dev, mom, ex, static_cast<float*>(p), (long long)c->n);
   }
@@ -583,30 +678,40 @@ lbm_status enqueue_window(lbm_ctx* c) {
   const int K = k.ckpt_every, S = c->lay.nslots;
   const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
   const size_t lat_bytes = c->q * c->n * c->rs;
+  const int64_t k0 = c->kernels;
   for (int s = 0; s < S; ++s) {
     cudaEvent_t e = c->begin();
     if (native) CUDA_TRY(cudaMemcpyAsync(c->seg_slot(s, 0), c->lattice(c->cur), lat_bytes, cudaMemcpyDeviceToDevice, c->ls));
     else c->impl->encode(c->lattice(c->cur), s);
     c->end(e, 3, 1, 0);
     e = c->begin();
-    for (int j = 0; j < K; ++j) {
-      const int step = s * K + j;
-      c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0);
-      c->cur ^= 1;
+    if (c->use_flow) {   // the K steps of the segment in one persistent launch
+      c->impl->fwd_run(c->lattice(c->cur), c->lattice(c->cur ^ 1), 0, K, s * K, k.sample_every);
+      c->cur ^= K & 1;
+    } else {
+      for (int j = 0; j < K; ++j) {
+        const int step = s * K + j;
+        c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0);
+        c->cur ^= 1;
+      }
     }
     c->end(e, 0, K, int64_t(K) * int64_t(c->n));
   }
   const double mon_scale =
       k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
   if (k.lattice == LBM_D2Q9) {
+    // persistent bands (single lattice only) sum as one flat run of block sums
     lbm::slice_end_kernel<<<k.nz, lbm::kEndThreads, 0, c->ls>>>(
         c->at<double>(c->lay.partials), c->lay.igx, c->lay.igy, c->lay.fbs, c->lay.igx * c->lay.igy * c->lay.igz,
         double(k.window_len / k.sample_every), c->at<double>(c->lay.slice_c), mon_scale, k.monitor_kind,
-        c->at<double>(c->lay.slice_j));
+        c->at<double>(c->lay.slice_j), c->use_flow ? c->lay.nblocks_sum : 0);
+    c->kernels += 1;
   }
   lbm::window_end_kernel<<<1, lbm::kEndThreads, 0, c->ls>>>(
-      c->at<double>(c->lay.partials), c->lay.nblocks_fwd, c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol,
+      c->at<double>(c->lay.partials), c->lay.nblocks_sum, c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol,
       c->at<int>(c->lay.flags), double(k.window_len / k.sample_every), c->jconst, mon_scale, k.monitor_kind);
+  c->kernels += 1;
+  c->kernels_window = c->kernels - k0;
   return LBM_OK;
 }
 
@@ -620,7 +725,10 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
   const lbm_config& k = c->cfg;
   const int K = k.ckpt_every, S = c->lay.nslots;
   const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
-  const bool pipe = c->lay.seg_sets == 2;
+  const bool flow = c->use_flow;
+  const bool pipe = c->lay.seg_sets == 2 && !flow;   // persistent launches own the whole GPU: serial
+  const size_t lat = align_up(c->q * c->n * c->rs);
+  const int64_t k0 = c->kernels;
   CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gacc), 0, c->n * 16, c->ls));
   CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gpart), 0, c->n * c->rs, c->ls));
   cudaStream_t main = c->ls;
@@ -635,7 +743,11 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
     if (!native) c->impl->decode(s, c->seg_slot(s, 0));
     c->end(e, 3, native ? 0 : 1, 0);
     e = c->begin();
-    for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
+    if (flow) {
+      if (K > 1) c->impl->fwd_run(c->seg_slot(s, 0), c->seg_slot(s, 1), lat, K - 1, 0, 0);
+    } else {
+      for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
+    }
     c->end(e, 1, K - 1, int64_t(K - 1) * int64_t(c->n));
   };
   if (pipe) {
@@ -662,15 +774,120 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
       cudaStreamWaitEvent(main, c->rec_done[s & 1], 0);
     }
     cudaEvent_t e = c->begin();
-    for (int j = K - 1; j >= 0; --j) {
-      const int step = s * K + j;
-      c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), step % k.sample_every == 0);
-      bnext = c->adjbuf(bo);
-      bo ^= 1;
+    if (flow) {   // step s K + j for j = K-1 .. 0 in one persistent launch
+      c->impl->adj_run(c->seg_slot(s, 0), K > 1 ? c->seg_slot(s, 1) : nullptr, lat, bnext, c->adjbuf(bo),
+                       c->adjbuf(bo ^ 1), K, s * K);
+      bnext = c->adjbuf(bo ^ ((K - 1) & 1));
+      bo ^= K & 1;
+    } else {
+      for (int j = K - 1; j >= 0; --j) {
+        const int step = s * K + j;
+        c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), step % k.sample_every == 0);
+        bnext = c->adjbuf(bo);
+        bo ^= 1;
+      }
     }
     c->end(e, 2, K, int64_t(K) * int64_t(c->n));
     c->impl->fold();
     if (pipe) cudaEventRecord(c->adj_done[s & 1], main);
+  }
+  c->kernels_adjoint = c->kernels - k0;
+  return LBM_OK;
+}
+
+// Schedule of the persistent step kernels (flow.cuh): P bands of consecutive
+// node indices, cut where the running cost crosses b/P of the total (a face
+// node costs kFaceCost interior nodes: a table gather and boundary rule), the
+// face-table rows of each band, and each band's wait set W(b) = deps(b) u
+// rdeps(b) \ {b}, where deps(b) holds every band that a node of b pulls from
+// (forward) or pushes to (adjoint).  Interior nodes never wrap, so their reads
+// lie within the largest lattice offset of the band; face nodes list theirs
+// in the table.  P starts at the number of co-resident blocks and halves
+// until every wait set fits.  The schedule is for a single lattice: D2Q9
+// batches keep the per-step kernels.
+template <class L>
+lbm_status build_flow(lbm_ctx* c, const std::vector<unsigned>& idx, const std::vector<unsigned>& src,
+                      const std::vector<unsigned>& dst, const std::vector<unsigned>& ext) {
+  const lbm_config& k = c->cfg;
+  c->flow_bands = 0;
+  if (L::D == 2 && k.nz != 1) return LBM_OK;
+  int P = c->impl->flow_capacity();
+  const size_t n = c->n;
+  const size_t per_block = lbm::kFlowBlock;
+  if (size_t(P) > (n + per_block - 1) / per_block) P = int((n + per_block - 1) / per_block);
+  if (P > lbm::kFlowMaxBands) P = lbm::kFlowMaxBands;
+  if (P < 1) return LBM_OK;
+  const unsigned nf = c->lay.nface;
+  size_t nreal = 0;   // face rows with a node (padding, if any, sits at the end)
+  while (nreal < idx.size() && idx[nreal] != lbm::kNone) ++nreal;
+  const bool d3 = L::D == 3;
+  auto is_face = [&](size_t i) {
+    const size_t x = i % k.nx, y = (i / k.nx) % k.ny, z = i / (size_t(k.nx) * k.ny);
+    return x == 0 || x == size_t(k.nx) - 1 || y == 0 || y == size_t(k.ny) - 1 ||
+           (d3 && (z == 0 || z == size_t(k.nz) - 1));
+  };
+  constexpr double kFaceCost = 3.0;
+  const double total = double(n) + (kFaceCost - 1.0) * double(nreal);
+  const size_t reach = d3 ? size_t(k.nx) * k.ny + k.nx + 1 : size_t(k.nx) + 1;
+  for (; P >= 1; P /= 2) {
+    std::vector<unsigned> band(size_t(P) + 1), fband(size_t(P) + 1);
+    band[0] = 0;
+    {
+      double run = 0.0;
+      int b = 1;
+      for (size_t i = 0; i < n && b < P; ++i) {
+        while (b < P && run >= total * double(b) / double(P)) band[size_t(b++)] = unsigned(i);
+        run += is_face(i) ? kFaceCost : 1.0;
+      }
+      while (b < P) band[size_t(b++)] = unsigned(n);
+      band[size_t(P)] = unsigned(n);
+    }
+    for (int b = 0; b <= P; ++b)
+      fband[size_t(b)] = unsigned(std::lower_bound(idx.begin(), idx.begin() + nreal, band[size_t(b)]) - idx.begin());
+    auto band_of = [&](unsigned i) {
+      return int(std::upper_bound(band.begin(), band.end(), i) - band.begin()) - 1;
+    };
+    std::vector<std::vector<int>> deps(static_cast<size_t>(P));
+    for (int b = 0; b < P; ++b) {
+      std::vector<int>& d = deps[size_t(b)];
+      const unsigned lo = band[size_t(b)], hi = band[size_t(b) + 1];
+      if (lo == hi) continue;
+      const unsigned rlo = lo > reach ? unsigned(lo - reach) : 0u;
+      const unsigned rhi = size_t(hi) + reach < n ? unsigned(hi + reach) : unsigned(n);
+      for (int t = band_of(rlo); t < P && band[size_t(t)] < rhi; ++t) d.push_back(t);
+      for (unsigned r = fband[size_t(b)]; r < fband[size_t(b) + 1]; ++r)
+        for (int a = 0; a < L::Q; ++a)
+          for (unsigned j : {src[size_t(a) * nf + r], dst[size_t(a) * nf + r], ext[size_t(a) * nf + r]})
+            if (j != lbm::kNone) d.push_back(band_of(j));
+    }
+    std::vector<std::vector<int>> wait(static_cast<size_t>(P));
+    for (int b = 0; b < P; ++b)
+      for (int t : deps[size_t(b)])
+        if (t != b) {
+          wait[size_t(b)].push_back(t);
+          wait[size_t(t)].push_back(b);
+        }
+    bool fits = true;
+    std::vector<int> wptr(size_t(P) + 1, 0), widx;
+    for (int b = 0; b < P && fits; ++b) {
+      std::vector<int>& w = wait[size_t(b)];
+      std::sort(w.begin(), w.end());
+      w.erase(std::unique(w.begin(), w.end()), w.end());
+      if (w.size() > size_t(lbm::kFlowMaxWait)) fits = false;
+      widx.insert(widx.end(), w.begin(), w.end());
+      wptr[size_t(b) + 1] = int(widx.size());
+    }
+    if (!fits) continue;
+    cudaStream_t s = c->stream;
+    const Layout& lay = c->lay;
+    CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_band), band.data(), band.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_fband), fband.data(), fband.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_wptr), wptr.data(), wptr.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!widx.empty())
+      CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_widx), widx.data(), widx.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    c->flow_bands = P;
+    return LBM_OK;
   }
   return LBM_OK;
 }
@@ -753,6 +970,7 @@ lbm_status build_face_table(lbm_ctx* c, const uint8_t* cls, const float* inlet_u
   }
   if (!d3) pad_to(nf);
   if (idx.size() != nf) return fail(LBM_ERR_ARG, "face count mismatch");
+  LBM_TRY(build_flow<L>(c, idx, src, dst, ext));
   cudaStream_t s = c->stream;
   CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_idx), idx.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_info), info.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
@@ -873,7 +1091,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   const size_t n = ctx->n;
   cudaStream_t s = ctx->stream;
   CUDA_TRY(cudaMemsetAsync(x->at(lay.f[0]), 0, align_up(ctx->q * n * ctx->rs), s));   // rest equilibrium
-  CUDA_TRY(cudaMemsetAsync(x->at(lay.partials), 0, size_t(lay.nblocks_fwd) * 32, s));
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.partials), 0, size_t(lay.nblocks_sum) * 32, s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.acc), 0, sizeof(lbm::WindowAcc), s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.flags), 0, 16, s));
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.cls), node_class, n, cudaMemcpyDefault, s));
@@ -963,6 +1181,12 @@ lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window)
   if (c->use_graphs) c->harvest_graph(c->gwin[cur0][c->timing ? 1 : 0]);
   c->harvest();
   c->steps += k.window_len;
+  if (acc.stalled) {
+    CUDA_TRY(cudaMemsetAsync(c->at<int>(c->lay.flags) + 2, 0, sizeof(int), c->stream));
+    c->window_valid = false;
+    c->grad_valid = false;
+    return fail(LBM_ERR_CUDA, "a persistent step kernel timed out waiting for a neighbouring band");
+  }
   if (acc.nonfinite) {
     c->window_valid = false;
     c->grad_valid = false;
@@ -1019,6 +1243,10 @@ lbm_status lbm_adjoint_window(lbm_ctx* c, double* J_eff) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (G) c->harvest_graph(*G);
   c->harvest();
+  if (c->use_flow) {
+    c->grad_valid = false;
+    LBM_TRY(check_flags(c, 2, LBM_ERR_CUDA, "a persistent step kernel timed out waiting for a neighbouring band"));
+  }
   // The sweep runs an even or odd number of adjoint steps: b^{n0} is in buffer (W-1) & 1.
   c->bout_last = (c->cfg.window_len - 1) & 1;
   c->grad_valid = true;
@@ -1188,6 +1416,41 @@ lbm_status lbm_set_pdl(lbm_ctx* c, int32_t enable) {
     for (auto& g : c->gadj) c->drop_graph(g);
   }
   c->use_pdl = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_flow(lbm_ctx* c, int32_t enable) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (enable && c->flow_bands == 0)
+    return fail(LBM_ERR_ARG, "persistent step kernels are unavailable here (D2Q9 batches, or no cooperative launch)");
+  if ((enable != 0) != c->use_flow) {
+    // captured graphs hold the other launch sequence: capture again on next use
+    for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);
+    for (auto& g : c->gadj) c->drop_graph(g);
+  }
+  c->use_flow = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_flow_test_hook(lbm_ctx* c, double wait_seconds, int32_t silent_band) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (!(wait_seconds > 0.0 && wait_seconds <= 60.0)) return fail(LBM_ERR_ARG, "wait_seconds must be in (0, 60]");
+  if (silent_band < -1 || silent_band >= c->flow_bands) return fail(LBM_ERR_ARG, "silent_band out of range");
+  for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);   // graphs hold the old parameters
+  for (auto& g : c->gadj) c->drop_graph(g);
+  c->flow_wait_ns = static_cast<unsigned long long>(wait_seconds * 1e9);
+  c->flow_silent = silent_band;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_schedule(lbm_ctx* c, lbm_schedule* out) {
+  if (!c || !out) return fail(LBM_ERR_ARG, "null argument");
+  out->flow_bands = c->flow_bands;
+  out->flow = c->use_flow ? 1 : 0;
+  out->graphs = c->use_graphs ? 1 : 0;
+  out->pdl = c->use_pdl ? 1 : 0;
+  out->kernels_window = c->kernels_window;
+  out->kernels_adjoint = c->kernels_adjoint;
   return LBM_OK;
 }
 

@@ -34,15 +34,18 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layouts_match_the_c_compiler(lib, tmp_path):
-    """Offsets of every field of lbm_config / lbm_timing as gcc lays them out
-    from the header equal the ctypes mirror's."""
+    """Offsets of every field of lbm_config / lbm_timing / lbm_schedule as gcc
+    lays them out from the header equal the ctypes mirror's."""
     fields = [f for f, _ in B.LbmConfig._fields_]
     tfields = [f for f, _ in B.LbmTiming._fields_]
+    sfields = [f for f, _ in B.LbmSchedule._fields_]
     prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbmadj.h"', "int main(void){"]
     prog.append('printf("%zu\\n", sizeof(lbm_config));')
     prog += [f'printf("%zu\\n", offsetof(lbm_config, {f}));' for f in fields]
     prog.append('printf("%zu\\n", sizeof(lbm_timing));')
     prog += [f'printf("%zu\\n", offsetof(lbm_timing, {f}));' for f in tfields]
+    prog.append('printf("%zu\\n", sizeof(lbm_schedule));')
+    prog += [f'printf("%zu\\n", offsetof(lbm_schedule, {f}));' for f in sfields]
     prog.append("return 0;}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(prog))
@@ -51,6 +54,7 @@ def test_struct_layouts_match_the_c_compiler(lib, tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(B.LbmConfig)] + [getattr(B.LbmConfig, f).offset for f in fields]
     want += [ctypes.sizeof(B.LbmTiming)] + [getattr(B.LbmTiming, f).offset for f in tfields]
+    want += [ctypes.sizeof(B.LbmSchedule)] + [getattr(B.LbmSchedule, f).offset for f in sfields]
     assert got == want
 
 

@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--graphs", type=int, default=1, help="replay windows / sweeps as CUDA graphs")
     ap.add_argument("--pipeline", type=int, default=1,
                     help="recompute the next segment while the adjoint sweeps the current one")
-    ap.add_argument("--pdl", type=int, default=0, help="programmatic dependent launch of the step kernels")
+    ap.add_argument("--pdl", type=int, default=1, help="programmatic dependent launch of the step kernels")
+    ap.add_argument("--tma", type=int, default=0,
+                    help="stage the interior forward steps' source rows in shared memory with TMA copies")
     ap.add_argument("--flow", type=int, default=0,
                     help="persistent launches: one cooperative kernel per checkpoint segment")
     ap.add_argument("--quick", action="store_true",
@@ -309,6 +311,8 @@ def run_ours(args, case, rank, world, local):
     sol.set_pdl(bool(args.pdl))
     if args.flow:
         sol.set_flow(True)
+    if args.tma:
+        sol.set_tma(True)
     n = case.n
     W, K = case.window_len, case.ckpt_every
     grad_dev = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -400,7 +404,8 @@ def run_ours(args, case, rank, world, local):
     # and adjoint steps may run concurrently.
     sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / len(sweep_ev)
     sweep_b = (bytes_per_lu(case, "adjoint", rs=rs) + bytes_per_lu(case, "recompute", rs=rs) * (K - 1) / K) * n
-    fk = "fwd_flow_kernel" if args.flow else "fwd_interior_kernel+fwd_face_kernel"
+    fk = ("fwd_flow_kernel" if args.flow else
+          "fwd_tma_kernel+fwd_face_kernel" if args.tma else "fwd_interior_kernel+fwd_face_kernel")
     ak = "adj_flow_kernel" if args.flow else "adj_interior_kernel+adj_face_kernel"
     units = {
         "forward step": {"bytes": bytes_per_lu(case, "forward", rs=rs) * n,
@@ -442,6 +447,8 @@ def run_ours(args, case, rank, world, local):
         if args.flow:
             s32.set_flow(True)
             ref.set_flow(True)
+        if args.tma:
+            s32.set_tma(True)
         ref.set_state(p)
         s32.set_state(p)
         J32, _ = s32.step_window()
@@ -482,7 +489,7 @@ def run_ours(args, case, rank, world, local):
                    "ckpt_format": ["fp32", "fp16", "bf16"][case.ckpt_format], "tau": case.tau,
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
                    "cuda_graphs": bool(args.graphs), "pipeline": bool(args.pipeline) and not args.flow,
-                   "pdl": bool(args.pdl), "persistent": bool(args.flow),
+                   "pdl": bool(args.pdl), "tma_staging": bool(args.tma), "persistent": bool(args.flow),
                    "persistent_bands": sched["flow_bands"] if args.flow else None,
                    "l2": "flushed (256 MB write) before every timed step; inside a step the forward "
                          "lattices (19 MB) stay L2-resident"},

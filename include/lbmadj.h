@@ -228,8 +228,8 @@ lbm_status lbm_get_timing(lbm_ctx* ctx, lbm_timing* out);
  * context's stream. */
 lbm_status lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
 
-/* Launch the step kernels with programmatic dependent launch (1) so that each
- * launch overlaps the tail of the previous one, or plainly (0, the default).
+/* Launch the step kernels with programmatic dependent launch (1, the default)
+ * so that each launch overlaps the tail of the previous one, or plainly (0).
  * Results are identical either way. */
 lbm_status lbm_set_pdl(lbm_ctx* ctx, int32_t enable);
 
@@ -249,6 +249,16 @@ lbm_status lbm_set_pdl(lbm_ctx* ctx, int32_t enable);
  * without cooperative launch. */
 lbm_status lbm_set_flow(lbm_ctx* ctx, int32_t enable);
 
+/* Stage the source rows of the interior forward steps (window and recompute)
+ * in shared memory with TMA bulk-tensor copies, several tiles ahead of the
+ * tile being computed (1), or load them straight into registers (0, the
+ * default).  The node arithmetic and the block sums are the same code, so
+ * results are bitwise identical.  Needs interior nodes and a row pitch
+ * (nx * element size) that is a multiple of 16 bytes: LBM_ERR_ARG otherwise.
+ * Copy waits are bounded; one that runs out fails the window or sweep with
+ * LBM_ERR_CUDA. */
+lbm_status lbm_set_tma(lbm_ctx* ctx, int32_t enable);
+
 /* Test hook of the persistent kernels' bounded waits: the longest wait without
  * progress (seconds, default 4) and one band that computes but never
  * publishes its progress (-1, the default: none), so that its neighbours'
@@ -262,6 +272,8 @@ typedef struct {
   int32_t flow;             /* 1: persistent segment launches (lbm_set_flow)          */
   int32_t graphs;           /* 1: windows and sweeps replay as CUDA graphs            */
   int32_t pdl;              /* 1: programmatic dependent launch                       */
+  int32_t tma_available;    /* 1: lbm_set_tma(ctx, 1) is accepted                     */
+  int32_t tma;              /* 1: TMA-staged interior forward steps (lbm_set_tma)     */
   int64_t kernels_window;   /* kernels enqueued by the last window (0 before one)     */
   int64_t kernels_adjoint;  /* kernels enqueued by the last adjoint sweep             */
 } lbm_schedule;

@@ -48,6 +48,7 @@ class LbmFilter(ctypes.Structure):
 
 class LbmSchedule(ctypes.Structure):
     _fields_ = [("flow_bands", c_int32), ("flow", c_int32), ("graphs", c_int32), ("pdl", c_int32),
+                ("tma_available", c_int32), ("tma", c_int32),
                 ("kernels_window", c_int64), ("kernels_adjoint", c_int64)]
 
 
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "lbm_set_graphs": (st, [c_void_p, c_int32]),
         "lbm_set_pdl": (st, [c_void_p, c_int32]),
         "lbm_set_flow": (st, [c_void_p, c_int32]),
+        "lbm_set_tma": (st, [c_void_p, c_int32]),
         "lbm_get_schedule": (st, [c_void_p, POINTER(LbmSchedule)]),
         "lbm_set_flow_test_hook": (st, [c_void_p, c_double, c_int32]),
         "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -278,6 +280,10 @@ class Solver:
     def set_flow(self, enable: bool):
         """Persistent segment launches (lbm_set_flow)."""
         check(lib().lbm_set_flow(self.ctx, int(bool(enable))), "lbm_set_flow")
+
+    def set_tma(self, enable: bool):
+        """TMA-staged interior forward steps (lbm_set_tma)."""
+        check(lib().lbm_set_tma(self.ctx, int(bool(enable))), "lbm_set_tma")
 
     def set_flow_test_hook(self, wait_seconds: float = 4.0, silent_band: int = -1):
         """Bounded-wait test hook of the persistent kernels (lbm_set_flow_test_hook)."""

@@ -70,6 +70,12 @@ struct Obj {
 };
 
 // Window-end results.
+// One block's compensated window sums: (j sum, j compensation, monitor sum,
+// monitor compensation); 32-byte aligned for one vector access.
+struct alignas(32) Sums {
+  double x, y, z, w;
+};
+
 struct WindowAcc {
   double jmean, mmean, mprev, ratio;
   int has_prev, converged, nonfinite;
@@ -376,10 +382,10 @@ __device__ __forceinline__ void block_sum2(R& a, R& b) {
 // cross-block step: the window-end kernel reduces the blocks in a fixed order.
 __device__ __forceinline__ void sample_commit(double bj, double bm, double* blk, unsigned bid) {
   if (threadIdx.x == 0) {
-    double4 a = reinterpret_cast<double4*>(blk)[bid];
+    Sums a = reinterpret_cast<Sums*>(blk)[bid];
     neumaier(a.x, a.y, bj);
     neumaier(a.z, a.w, bm);
-    reinterpret_cast<double4*>(blk)[bid] = a;
+    reinterpret_cast<Sums*>(blk)[bid] = a;
   }
 }
 
@@ -436,8 +442,34 @@ struct FwdStep {
   int sample;
 };
 
-// One node of a forward step (interior or face node); a sampled step adds the
-// node's objective and monitor terms to bj, bm.
+// Collision, blend, store and sample of one node whose pulled populations f
+// are loaded (Eqs. 12-16, 23, 24-25); a sampled step adds the node's
+// objective and monitor terms to bj, bm.
+template <class L, class R>
+__device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<R>& P, int x, int y, int z,
+                                             unsigned i, const R (&f)[L::Q], R& bj, R& bm) {
+  const Geo& g = A.geo;
+  Mom<L, R> M;
+  moments<L, R>(f, A.ph, M);
+  if (!(M.rho > R(0)) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
+  const R gi = A.gfield[i];
+  R a0, B[3], T[6];
+  post_collision<L, R>(M, gi, a0, B, T);
+  R* dst = P.dst;
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
+  if (P.sample) {
+    const int* b = A.obj.box;
+    if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
+      const R w = R(A.wobj[i]);
+      if (w != R(0)) bj += w * local_objective<L, R>(M, A.obj, gi);
+    }
+    if (A.obj.mon == MON_DRAG) bm += R(-2) * gi * M.m[0];
+  }
+}
+
+// One node of a forward step (interior or face node): pull (Eq. 7), complete
+// the boundary populations of a face node (Eqs. 19-21), then forward_core.
 // For a face node k is its row in the face table; for an interior node k is unused.
 // CG: the source field is written concurrently by other blocks of the launch.
 template <class L, class R, bool FACE, bool CG = false>
@@ -445,7 +477,6 @@ __device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<
                                              unsigned i, unsigned k, R& bj, R& bm) {
   const Geo& g = A.geo;
   const R* src = P.src;
-  R* dst = P.dst;
   R f[L::Q];
   if (FACE) {
     const FaceTable& t = A.ft;
@@ -457,22 +488,7 @@ __device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) f[a] = ldf<CG>(src + (a * g.n + i - offset<L>(g, a)));
   }
-  Mom<L, R> M;
-  moments<L, R>(f, A.ph, M);
-  if (!(M.rho > R(0)) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
-  const R gi = A.gfield[i];
-  R a0, B[3], T[6];
-  post_collision<L, R>(M, gi, a0, B, T);
-#pragma unroll
-  for (int a = 0; a < L::Q; ++a) dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
-  if (P.sample) {
-    const int* b = A.obj.box;
-    if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
-      const R w = R(A.wobj[i]);
-      if (w != R(0)) bj += w * local_objective<L, R>(M, A.obj, gi);
-    }
-    if (A.obj.mon == MON_DRAG) bm += R(-2) * gi * M.m[0];
-  }
+  forward_core<L, R>(A, P, x, y, z, i, f, bj, bm);
 }
 
 // Interior nodes: x in [1, nx-1), y in [1, ny-1), z in [1, nz-1) (3D).  No
@@ -521,12 +537,12 @@ __global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, in
   __shared__ double sh[4][kEndThreads];
   double sj = 0, cj = 0, sm = 0, cm = 0;
   for (int b = threadIdx.x; b < nblocks; b += kEndThreads) {
-    double4 a = reinterpret_cast<double4*>(blk)[b];
+    Sums a = reinterpret_cast<Sums*>(blk)[b];
     neumaier(sj, cj, a.x);
     neumaier(sj, cj, a.y);
     neumaier(sm, cm, a.z);
     neumaier(sm, cm, a.w);
-    reinterpret_cast<double4*>(blk)[b] = make_double4(0.0, 0.0, 0.0, 0.0);
+    reinterpret_cast<Sums*>(blk)[b] = Sums{0.0, 0.0, 0.0, 0.0};
   }
   // Fixed-shape tree over the threads' (sum, compensation) pairs: deterministic.
   const int t = threadIdx.x;
@@ -576,7 +592,7 @@ __global__ void __launch_bounds__(kEndThreads) slice_end_kernel(const double* bl
   double sj = 0, cj = 0, sm = 0, cm = 0;
   for (int b = t; b < count; b += kEndThreads) {
     const int bid = nflat > 0 ? b : b < nib ? slice * nib + b : nint + slice * fbs + (b - nib);
-    const double4 a = reinterpret_cast<const double4*>(blk)[bid];
+    const Sums a = reinterpret_cast<const Sums*>(blk)[bid];
     neumaier(sj, cj, a.x);
     neumaier(sj, cj, a.y);
     neumaier(sm, cm, a.z);

@@ -9,6 +9,8 @@
 // native checkpoints), then runs K adjoint launches from the last state to
 // the first.  The design sensitivity of every adjoint step is added into a
 // per-node FP64 (sum, compensation) pair.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,12 +20,14 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "lbmadj.h"
 #include "filter.cuh"
 #include "flow.cuh"
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -233,6 +237,7 @@ struct Impl {
   virtual void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every) = 0;
   virtual void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
                        int nsteps, int step0) = 0;
+  virtual bool tma_setup() = 0;      // encoder and launch shape of the TMA-staged kernels
 };
 
 // A captured CUDA graph with the timing events its replays record.
@@ -257,7 +262,9 @@ struct lbm_ctx {
   cudaStream_t side_cur = nullptr;        // side stream / events of the stream now in ls
   cudaEvent_t fork_cur = nullptr, join_cur = nullptr;
   bool use_graphs = true;
-  bool use_pdl = false;
+  bool use_pdl = true;        // programmatic dependent launch of the step kernels
+  bool tma_ok = false;        // TMA-staged interior kernels available (row pitch a multiple of 16 bytes)
+  bool use_tma = false;       // forward interior steps through fwd_tma_kernel
   int flow_bands = 0;         // bands of the persistent schedule (0: not available)
   bool use_flow = false;      // run segments as persistent launches
   unsigned long long flow_wait_ns = 4000000000ull;   // 4 s without progress of a neighbouring band
@@ -480,8 +487,76 @@ struct ImplT final : Impl {
   void fwd(const void* src, void* dst, int sample) override {
     const lbm::FwdArgs<R> A = fwd_args(src, dst, sample);
     const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
-    fork_join([&](cudaStream_t st) { launch(lbm::fwd_interior_kernel<L, R>, igrid(), st, A); },
-              [&](cudaStream_t st) { launch(lbm::fwd_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A, blk0); });
+    const CUtensorMap* map = c->use_tma ? tensor_map(src) : nullptr;
+    fork_join(
+        [&](cudaStream_t st) {
+          if (map) launch_tma(lbm::fwd_tma_kernel<L, R>, st, *map, A, blk0, unsigned(c->lay.igx),
+                              unsigned(c->lay.igy), c->template at<int>(c->lay.flags) + 2);
+          else launch(lbm::fwd_interior_kernel<L, R>, igrid(), st, A);
+        },
+        [&](cudaStream_t st) { launch(lbm::fwd_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A, blk0); });
+  }
+
+  // TMA-staged interior kernels (tma.cuh).
+  PFN_cuTensorMapEncodeTiled_v12000 encode_map = nullptr;
+  std::unordered_map<const void*, CUtensorMap> maps;
+  int tma_grid = 0;
+  bool tma_setup() override {
+    const lbm_config& k = c->cfg;
+    if (!has_interior() || (size_t(k.nx) * sizeof(R)) % 16 != 0) return false;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode_map = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const size_t smem = lbm::fwd_tma_smem<L, R>();
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaFuncSetAttribute(lbm::fwd_tma_kernel<L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::fwd_tma_kernel<L, R>, lbm::kBlock, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    const long long tiles = (long long)c->lay.igx * c->lay.igy * c->lay.igz;
+    tma_grid = int(std::min<long long>(tiles, (long long)sms * per_sm));
+    return tensor_map(c->lattice(0)) != nullptr;
+  }
+  // The tensor map of a population field at base: {nx, ny, nz Q}, one box of
+  // kTmaBox x 1 x 1 elements.  Encoded once per field address.
+  const CUtensorMap* tensor_map(const void* base) {
+    auto it = maps.find(base);
+    if (it != maps.end()) return &it->second;
+    const lbm_config& k = c->cfg;
+    CUtensorMap m;
+    const cuuint64_t dims[3] = {cuuint64_t(k.nx), cuuint64_t(k.ny), cuuint64_t(k.nz) * L::Q};
+    const cuuint64_t strides[2] = {cuuint64_t(k.nx) * sizeof(R), cuuint64_t(k.nx) * k.ny * sizeof(R)};
+    const cuuint32_t box[3] = {cuuint32_t(lbm::kTmaBox), 1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode_map(&m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                  3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nullptr;
+    return &maps.emplace(base, m).first->second;
+  }
+  template <class... Args>
+  void launch_tma(void (*kernel)(const CUtensorMap, Args...), cudaStream_t st, const CUtensorMap& map, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tma_grid);
+    cfg.blockDim = dim3(lbm::kBlock);
+    cfg.dynamicSmemBytes = lbm::fwd_tma_smem<L, R>();
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->use_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, map, args...);
   }
   void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
     const lbm::AdjArgs<R> A = adj_args(bnext, pprev, bout, sample);
@@ -1156,6 +1231,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   x->impl->set_design();
   CUDA_TRY(cudaGetLastError());
   LBM_TRY(check_flags(x, 1, LBM_ERR_ARG, "design values must lie in [0, 1]"));
+  x->tma_ok = x->impl->tma_setup();
   *out = ctx.release();
   return LBM_OK;
 }
@@ -1185,7 +1261,7 @@ lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window)
     CUDA_TRY(cudaMemsetAsync(c->at<int>(c->lay.flags) + 2, 0, sizeof(int), c->stream));
     c->window_valid = false;
     c->grad_valid = false;
-    return fail(LBM_ERR_CUDA, "a persistent step kernel timed out waiting for a neighbouring band");
+    return fail(LBM_ERR_CUDA, "a step kernel timed out waiting (for a neighbouring band or a TMA copy)");
   }
   if (acc.nonfinite) {
     c->window_valid = false;
@@ -1243,9 +1319,9 @@ lbm_status lbm_adjoint_window(lbm_ctx* c, double* J_eff) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (G) c->harvest_graph(*G);
   c->harvest();
-  if (c->use_flow) {
+  if (c->use_flow || c->use_tma) {
     c->grad_valid = false;
-    LBM_TRY(check_flags(c, 2, LBM_ERR_CUDA, "a persistent step kernel timed out waiting for a neighbouring band"));
+    LBM_TRY(check_flags(c, 2, LBM_ERR_CUDA, "a step kernel timed out waiting (for a neighbouring band or a TMA copy)"));
   }
   // The sweep runs an even or odd number of adjoint steps: b^{n0} is in buffer (W-1) & 1.
   c->bout_last = (c->cfg.window_len - 1) & 1;
@@ -1432,6 +1508,18 @@ lbm_status lbm_set_flow(lbm_ctx* c, int32_t enable) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_tma(lbm_ctx* c, int32_t enable) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (enable && !c->tma_ok)
+    return fail(LBM_ERR_ARG, "TMA staging needs an interior and nx * element size a multiple of 16 bytes");
+  if ((enable != 0) != c->use_tma) {
+    for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);
+    for (auto& g : c->gadj) c->drop_graph(g);
+  }
+  c->use_tma = enable != 0;
+  return LBM_OK;
+}
+
 lbm_status lbm_set_flow_test_hook(lbm_ctx* c, double wait_seconds, int32_t silent_band) {
   if (!c) return fail(LBM_ERR_ARG, "null context");
   if (!(wait_seconds > 0.0 && wait_seconds <= 60.0)) return fail(LBM_ERR_ARG, "wait_seconds must be in (0, 60]");
@@ -1449,6 +1537,8 @@ lbm_status lbm_get_schedule(lbm_ctx* c, lbm_schedule* out) {
   out->flow = c->use_flow ? 1 : 0;
   out->graphs = c->use_graphs ? 1 : 0;
   out->pdl = c->use_pdl ? 1 : 0;
+  out->tma_available = c->tma_ok ? 1 : 0;
+  out->tma = c->use_tma ? 1 : 0;
   out->kernels_window = c->kernels_window;
   out->kernels_adjoint = c->kernels_adjoint;
   return LBM_OK;

@@ -36,6 +36,7 @@ for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
 
 METRIC = "forward & adjoint MLUPS and % HBM roofline, FP32/mixed vs FP64 at stated error"
 WORKLOAD = "wake1024x256"
+CKPT_NAMES = ["fp32", "fp16", "bf16", "moment"]   # lbm_config.ckpt_format
 KERNEL_SRC = os.path.join(ROOT, "paper_2608_19617_b300", "csrc", "kernels.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -54,6 +55,8 @@ def parse():
     ap.add_argument("--spinup-windows", type=int, default=20,
                     help="spin-up: windows of Alg. 1 until Eq. 26 holds, at most this many")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--ckpt-format", default="", choices=[""] + CKPT_NAMES,
+                    help="override the workload's checkpoint format")
     ap.add_argument("--graphs", type=int, default=1, help="replay windows / sweeps as CUDA graphs")
     ap.add_argument("--pipeline", type=int, default=1,
                     help="recompute the next segment while the adjoint sweeps the current one")
@@ -462,7 +465,7 @@ def run_ours(args, case, rank, world, local):
         err = {"J_rel_err_fp32_vs_fp64": abs(J32 - J64) / abs(J64), "grad_cosine_fp32_vs_fp64": cos,
                "grad_rel_err_fp32_vs_fp64": float(np.linalg.norm(g32 - g64) / n64) if n64 > 0 else None,
                "grad_norm_fp64": n64,
-               "window_len": W_err, "fp32_ckpt": ["fp32", "fp16", "bf16"][c32.ckpt_format],
+               "window_len": W_err, "fp32_ckpt": CKPT_NAMES[c32.ckpt_format],
                "fp64_ckpt_every": K_err}
         ref.close()
         if s32 is not sol:
@@ -486,7 +489,7 @@ def run_ours(args, case, rank, world, local):
         "config": {"workload": case.name, "lattice": f"D{2 if case.lattice == 9 else 3}Q{case.lattice}",
                    "nx": case.nx, "ny": case.ny, "nz": case.nz,
                    "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
-                   "ckpt_format": ["fp32", "fp16", "bf16"][case.ckpt_format], "tau": case.tau,
+                   "ckpt_format": CKPT_NAMES[case.ckpt_format], "tau": case.tau,
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
                    "cuda_graphs": bool(args.graphs), "pipeline": bool(args.pipeline) and not args.flow,
                    "pdl": bool(args.pdl), "tma_staging": bool(args.tma), "persistent": bool(args.flow),
@@ -516,6 +519,8 @@ def main():
     if args.window_len or args.ckpt_every:
         wl = args.window_len or case.window_len
         case = case.replace(window_len=wl, ckpt_every=args.ckpt_every or wl)
+    if args.ckpt_format:
+        case = case.replace(ckpt_format=CKPT_NAMES.index(args.ckpt_format))
     if args.impl == "reference":
         rc = run_reference(args, case, rank, world)
         return rc

@@ -78,10 +78,19 @@ enum { LBM_OBJ_DISSIPATION = 0, LBM_OBJ_VELOCITY_DEV = 1, LBM_OBJ_PRESSURE = 2, 
  * sum_i sum_a c_xa F_a / (rho_out monitor_u^2 monitor_l / 2), or j itself. */
 enum { LBM_MON_DRAG = 0, LBM_MON_OBJECTIVE = 1 };
 
-/* Checkpoint storage for the adjoint's recompute: the working precision, or
- * the deviation from equilibrium in FP16/BF16 with one power-of-two scale per
- * block of nodes plus FP32 density and momentum (lossy; FP32 solver only). */
-enum { LBM_CKPT_NATIVE = 0, LBM_CKPT_FP16 = 1, LBM_CKPT_BF16 = 2 };
+/* Checkpoint storage for the adjoint's recompute:
+ *  NATIVE: the carried field in the working precision (Q values per node).
+ *  FP16, BF16: the deviation from equilibrium in 16 bits with one power-of-two
+ *        scale per block of nodes plus FP32 density and momentum (lossy; FP32
+ *        solver only).
+ *  MOMENT: lossless and smaller (a library design with no counterpart in the
+ *        paper).  Every carried value is p~_a = w_a (A + B.c_a + c_a.T.c_a)
+ *        with one scalar A, vector B and symmetric tensor T per node (the
+ *        regularized collision and blend of Eqs. 16 and 23), so checkpoints
+ *        1 .. S-1 keep those 6 (2D) or 10 (3D) values, stored by the step that
+ *        produces the field, and regenerate it bitwise.  Checkpoint 0, the
+ *        window's start field, which need not come from a step, stays native. */
+enum { LBM_CKPT_NATIVE = 0, LBM_CKPT_FP16 = 1, LBM_CKPT_BF16 = 2, LBM_CKPT_MOMENT = 3 };
 
 typedef struct {
   int32_t lattice;          /* LBM_D2Q9 or LBM_D3Q19                                  */
@@ -253,7 +262,8 @@ lbm_status lbm_set_flow(lbm_ctx* ctx, int32_t enable);
  * in shared memory with TMA bulk-tensor copies, several tiles ahead of the
  * tile being computed (1), or load them straight into registers (0, the
  * default).  The node arithmetic and the block sums are the same code, so
- * results are bitwise identical.  Needs interior nodes and a row pitch
+ * results agree to a few units in the last place (the compiler may fuse
+ * multiply-adds differently in the two kernels).  Needs interior nodes and a row pitch
  * (nx * element size) that is a multiple of 16 bytes: LBM_ERR_ARG otherwise.
  * Copy waits are bounded; one that runs out fails the window or sweep with
  * LBM_ERR_CUDA. */

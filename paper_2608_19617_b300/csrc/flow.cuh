@@ -151,8 +151,8 @@ __device__ __noinline__ void adj_face_node(const AdjArgs<R>& A, const AdjStep<R>
 // Forward steps step0 .. step0+nsteps-1 of a window (or of a recompute when
 // sample_every == 0: nothing is sampled).
 template <class L, class R>
-__global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 1) fwd_flow_kernel(FwdArgs<R> A, Chain<R> ch, Flow fl, int nsteps,
-                                                              int step0, int sample_every) {
+__global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 1)
+    fwd_flow_kernel(FwdArgs<R> A, Chain<R> ch, Flow fl, int nsteps, int step0, int sample_every) {
   const Geo& g = A.geo;
   const unsigned b = blockIdx.x;
   const unsigned i0 = fl.band[b], i1 = fl.band[b + 1], f0 = fl.fband[b], f1 = fl.fband[b + 1];
@@ -161,7 +161,9 @@ __global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 
 #pragma unroll 1
   for (int k = 0; k < nsteps; ++k) {
     if (k > 0 && !flow_wait(fl, b, k)) break;
-    const FwdStep<R> P{ch.src(k), ch.dst(k), sample_every > 0 && (step0 + k) % sample_every == 0};
+    // A.mom: moment checkpoint of the launch's last output
+    const FwdStep<R> P{ch.src(k), ch.dst(k), sample_every > 0 && (step0 + k) % sample_every == 0,
+                       k == nsteps - 1 ? A.mom : nullptr};
     R bj = 0, bm = 0;
     int x = x0, y = y0, z = z0;
 #pragma unroll 1
@@ -195,8 +197,8 @@ struct AdjChain {
 };
 
 template <class L, class R>
-__global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 1) adj_flow_kernel(AdjArgs<R> A, AdjChain<R> ch, Flow fl, int nsteps,
-                                                              int step0, int sample_every) {
+__global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 1)
+    adj_flow_kernel(AdjArgs<R> A, AdjChain<R> ch, Flow fl, int nsteps, int step0, int sample_every) {
   const Geo& g = A.geo;
   const unsigned b = blockIdx.x;
   const unsigned i0 = fl.band[b], i1 = fl.band[b + 1], f0 = fl.fband[b], f1 = fl.fband[b + 1];

@@ -340,19 +340,26 @@ __device__ __forceinline__ R quad_form(int a, R s0, const R (&s1)[3], const R (&
 //        = w_a (A + 3 m.c_a + c_a.T.c_a),
 //   A = rho - 1 - 1.5 m.u - 1.5 om tr(Pi),  T = 4.5 (m u^T + om Pi),
 // and the blend scales the odd part: p~_a = w_a (A + 3 (1 - 2g) m.c_a + c_a.T.c_a).
+//
+// B and T are formed with rounded multiplies that the compiler may not fuse
+// into the additions of quad_form: the coefficients a step adds are then
+// exactly the rounded values a moment checkpoint stores.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <class L, class R>
 __device__ __forceinline__ void post_collision(const Mom<L, R>& M, R g, R& A, R (&B)[3], R (&T)[6]) {
   const R tr = M.pi[0] + M.pi[1] + M.pi[2];
   A = M.rt - R(1.5) * (M.m[0] * M.u[0] + M.m[1] * M.u[1] + M.m[2] * M.u[2]) - R(1.5) * M.om * tr;
   const R b = R(3) * (R(1) - R(2) * g);
-  B[0] = b * M.m[0]; B[1] = b * M.m[1]; B[2] = b * M.m[2];
+  B[0] = mul_rn(b, M.m[0]); B[1] = mul_rn(b, M.m[1]); B[2] = mul_rn(b, M.m[2]);
   const R k = R(4.5);
-  T[0] = k * (M.m[0] * M.u[0] + M.om * M.pi[0]);
-  T[1] = k * (M.m[1] * M.u[1] + M.om * M.pi[1]);
-  T[2] = k * (M.m[2] * M.u[2] + M.om * M.pi[2]);
-  T[3] = k * (M.m[0] * M.u[1] + M.om * M.pi[3]);
-  T[4] = k * (M.m[0] * M.u[2] + M.om * M.pi[4]);
-  T[5] = k * (M.m[1] * M.u[2] + M.om * M.pi[5]);
+  T[0] = mul_rn(k, M.m[0] * M.u[0] + M.om * M.pi[0]);
+  T[1] = mul_rn(k, M.m[1] * M.u[1] + M.om * M.pi[1]);
+  T[2] = mul_rn(k, M.m[2] * M.u[2] + M.om * M.pi[2]);
+  T[3] = mul_rn(k, M.m[0] * M.u[1] + M.om * M.pi[3]);
+  T[4] = mul_rn(k, M.m[0] * M.u[2] + M.om * M.pi[4]);
+  T[5] = mul_rn(k, M.m[1] * M.u[2] + M.om * M.pi[5]);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,6 +418,7 @@ struct FwdArgs {
   double* blk;                   // per-block window sums (4 doubles per block)
   int* nonfinite;
   FaceTable ft;
+  R* mom;                        // non-null: also store the step's collision coefficients (moment checkpoint)
 };
 
 template <class L, class R>
@@ -440,7 +448,32 @@ struct FwdStep {
   const R* src;   // p^{n-1}
   R* dst;         // p^n
   int sample;
+  R* mom;         // non-null: moment checkpoint of p^n (mom_coefs<L>() planes of n values)
 };
+
+// Moment checkpoints.  The carried field is p~_a = w_a (A + B.c_a + c_a.T.c_a)
+// at every node (interior and face alike), so the FP32 (or FP64) values of A,
+// B and T as the step computed them regenerate p~ exactly: 1 + D + D(D+1)/2
+// planes (6 in 2D, 10 in 3D) instead of Q.
+template <class L>
+__host__ __device__ constexpr int mom_coefs() { return L::D == 2 ? 6 : 10; }
+
+template <class L, class R>
+__device__ __forceinline__ void store_coefs(R* mom, unsigned n, unsigned i, R a0, const R (&B)[3], const R (&T)[6]) {
+  mom[i] = a0;
+  if (L::D == 2) {
+    mom[n + i] = B[0];
+    mom[2 * n + i] = B[1];
+    mom[3 * n + i] = T[0];
+    mom[4 * n + i] = T[1];
+    mom[5 * n + i] = T[3];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mom[(1 + k) * n + i] = B[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mom[(4 + k) * n + i] = T[k];
+  }
+}
 
 // Collision, blend, store and sample of one node whose pulled populations f
 // are loaded (Eqs. 12-16, 23, 24-25); a sampled step adds the node's
@@ -455,6 +488,7 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
   const R gi = A.gfield[i];
   R a0, B[3], T[6];
   post_collision<L, R>(M, gi, a0, B, T);
+  if (P.mom) store_coefs<L, R>(P.mom, g.n, i, a0, B, T);
   R* dst = P.dst;
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
@@ -501,7 +535,7 @@ __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
   const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
   R bj = 0, bm = 0;
   if (x < g.nx - 1)
-    forward_node<L, R, false>(A, FwdStep<R>{A.src, A.dst, A.sample}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
+    forward_node<L, R, false>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
   if (A.sample) {   // uniform across the grid
     block_sum2<R>(bj, bm);
     sample_commit(double(bj), double(bm), A.blk);
@@ -518,7 +552,7 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   const unsigned i = k < A.ft.n ? A.ft.idx[k] : kNone;   // rows padded per slice hold kNone
   if (i != kNone) {
     const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
-    forward_node<L, R, true>(A, FwdStep<R>{A.src, A.dst, A.sample}, x, y, z, i, k, bj, bm);
+    forward_node<L, R, true>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, k, bj, bm);
   }
   if (A.sample) {
     block_sum2<R>(bj, bm);
@@ -976,6 +1010,30 @@ __global__ void gradient_kernel(const double2* __restrict__ gacc, const float* _
     }
     out[i] = v;
   }
+}
+
+// Moment checkpoint -> p~ at every node: w_a (A + B.c_a + c_a.T.c_a) with the
+// same expression as the step kernels, so the field is bitwise the one stored.
+template <class L, class R>
+__global__ void __launch_bounds__(kBlock) mom_decode_kernel(const R* __restrict__ mom, R* __restrict__ p, unsigned n) {
+  const unsigned i = blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  R B[3] = {R(0), R(0), R(0)}, T[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  const R a0 = mom[i];
+  if (L::D == 2) {
+    B[0] = mom[n + i];
+    B[1] = mom[2 * n + i];
+    T[0] = mom[3 * n + i];
+    T[1] = mom[4 * n + i];
+    T[3] = mom[5 * n + i];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) B[k] = mom[(1 + k) * n + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) T[k] = mom[(4 + k) * n + i];
+  }
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) p[a * n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
 }
 
 template <class L, class R>

@@ -121,8 +121,8 @@ lbm_status validate_config(const lbm_config& c) {
   if (c.window_len < 1) return fail(LBM_ERR_ARG, "window_len must be >= 1");
   if (c.sample_every < 1 || c.window_len % c.sample_every) return fail(LBM_ERR_ARG, "sample_every must divide window_len");
   if (c.ckpt_every < 1 || c.window_len % c.ckpt_every) return fail(LBM_ERR_ARG, "ckpt_every must divide window_len");
-  if (c.ckpt_format < 0 || c.ckpt_format > 2) return fail(LBM_ERR_ARG, "ckpt_format out of range");
-  if (c.ckpt_format != LBM_CKPT_NATIVE && c.precision != LBM_FP32)
+  if (c.ckpt_format < 0 || c.ckpt_format > 3) return fail(LBM_ERR_ARG, "ckpt_format out of range");
+  if ((c.ckpt_format == LBM_CKPT_FP16 || c.ckpt_format == LBM_CKPT_BF16) && c.precision != LBM_FP32)
     return fail(LBM_ERR_ARG, "16-bit checkpoints need the FP32 solver");
   if (!(c.conv_tol >= 0.0)) return fail(LBM_ERR_ARG, "conv_tol must be >= 0");
   if (c.pipeline != 0 && c.pipeline != 1) return fail(LBM_ERR_ARG, "pipeline must be 0 or 1");
@@ -161,9 +161,12 @@ Layout make_layout(const lbm_config& c) {
   L.nblocks_1d = int((n + lbm::kBlock - 1) / lbm::kBlock);
   L.nslots = c.window_len / c.ckpt_every;
   const bool native = c.ckpt_format == LBM_CKPT_NATIVE;
-  L.ckpt_slot = native ? lat
-                       : align_up(size_t(q) * n * 2) + align_up(size_t(d + 1) * n * 4) +
-                             align_up(size_t(L.nblocks_1d) * 4);
+  const bool moment = c.ckpt_format == LBM_CKPT_MOMENT;
+  // moment checkpoints: slot 0 (the window's start field) native, slots 1.. the coefficient planes
+  L.ckpt_slot = native   ? lat
+                : moment ? align_up(size_t(d == 2 ? 6 : 10) * n * rs)
+                         : align_up(size_t(q) * n * 2) + align_up(size_t(d + 1) * n * 4) +
+                               align_up(size_t(L.nblocks_1d) * 4);
   L.seg_slots = native ? size_t(c.ckpt_every - 1) : size_t(c.ckpt_every);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
@@ -200,7 +203,7 @@ Layout make_layout(const lbm_config& c) {
   L.wfilt = take(n * 8);      // filter normalisation W_i
   L.acc = take(sizeof(lbm::WindowAcc));
   L.flags = take(16);
-  L.ckpt = take(L.ckpt_slot * L.nslots);
+  L.ckpt = take(moment ? lat + L.ckpt_slot * size_t(L.nslots - 1) : L.ckpt_slot * L.nslots);
   L.seg_sets = c.pipeline ? 2 : 1;
   L.seg = take(lat * L.seg_slots * L.seg_sets);
   const size_t stage_bytes = size_t(q) * n * 8;
@@ -221,7 +224,7 @@ struct Pending {
 // Polymorphic per-(lattice, precision) implementation.
 struct Impl {
   virtual ~Impl() = default;
-  virtual void fwd(const void* src, void* dst, int sample) = 0;
+  virtual void fwd(const void* src, void* dst, int sample, void* mom = nullptr) = 0;
   virtual void adj(const void* bnext, const void* pprev, void* bout, int sample) = 0;
   virtual void pull(const void* b, void* out) = 0;
   virtual void set_design() = 0;
@@ -234,7 +237,8 @@ struct Impl {
   virtual void decode(int slot, void* p) = 0;
   // Persistent step kernels (see flow.cuh).
   virtual int flow_capacity() = 0;   // co-resident blocks of the persistent kernels, 0 if none
-  virtual void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every) = 0;
+  virtual void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every,
+                       void* mom = nullptr) = 0;
   virtual void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
                        int nsteps, int step0) = 0;
   virtual bool tma_setup() = 0;      // encoder and launch shape of the TMA-staged kernels
@@ -305,7 +309,11 @@ struct lbm_ctx {
       if (j == 0) return ws + lay.ckpt + lay.ckpt_slot * s;
       return base + lat * (j - 1);
     }
+    if (cfg.ckpt_format == LBM_CKPT_MOMENT && s == 0 && j == 0) return ws + lay.ckpt;   // native slot 0
     return base + lat * j;
+  }
+  void* ckpt_mom(int s) const {   // moment checkpoint s >= 1
+    return ws + lay.ckpt + align_up(q * n * rs) + lay.ckpt_slot * size_t(s - 1);
   }
 
   cudaEvent_t event() {
@@ -448,8 +456,9 @@ struct ImplT final : Impl {
     return o;
   }
 
-  lbm::FwdArgs<R> fwd_args(const void* src, void* dst, int sample) const {
+  lbm::FwdArgs<R> fwd_args(const void* src, void* dst, int sample, void* mom = nullptr) const {
     lbm::FwdArgs<R> A;
+    A.mom = static_cast<R*>(mom);
     A.src = static_cast<const R*>(src);
     A.dst = static_cast<R*>(dst);
     A.gfield = c->template at<R>(c->lay.g);
@@ -484,8 +493,8 @@ struct ImplT final : Impl {
     A.ft = table();
     return A;
   }
-  void fwd(const void* src, void* dst, int sample) override {
-    const lbm::FwdArgs<R> A = fwd_args(src, dst, sample);
+  void fwd(const void* src, void* dst, int sample, void* mom) override {
+    const lbm::FwdArgs<R> A = fwd_args(src, dst, sample, mom);
     const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
     const CUtensorMap* map = c->use_tma ? tensor_map(src) : nullptr;
     fork_join(
@@ -608,8 +617,8 @@ struct ImplT final : Impl {
     cudaLaunchKernelEx(&cfg, kernel, args...);
     c->kernels += 1;
   }
-  void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every) override {
-    const lbm::FwdArgs<R> A = fwd_args(nullptr, nullptr, 0);
+  void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every, void* mom) override {
+    const lbm::FwdArgs<R> A = fwd_args(nullptr, nullptr, 0, mom);
     const lbm::Chain<R> ch{static_cast<R*>(a), static_cast<R*>(b), (long long)(stride_bytes / sizeof(R))};
     launch_flow(lbm::fwd_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, sample_every);
   }
@@ -685,6 +694,12 @@ struct ImplT final : Impl {
     }
   }
   void decode(int slot, void* p) override {
+    if (c->cfg.ckpt_format == LBM_CKPT_MOMENT) {
+      c->kernels += 1;
+      lbm::mom_decode_kernel<L, R><<<c->lay.nblocks_1d, lbm::kBlock, 0, c->ls>>>(
+          static_cast<const R*>(c->ckpt_mom(slot)), static_cast<R*>(p), unsigned(c->n));
+      return;
+    }
     if constexpr (sizeof(R) == 4) {
       if (c->cfg.ckpt_format == LBM_CKPT_FP16) decode_t<__half>(slot, p); else decode_t<__nv_bfloat16>(slot, p);
     }
@@ -752,21 +767,26 @@ lbm_status enqueue_window(lbm_ctx* c) {
   const lbm_config& k = c->cfg;
   const int K = k.ckpt_every, S = c->lay.nslots;
   const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
+  const bool moment = k.ckpt_format == LBM_CKPT_MOMENT;
   const size_t lat_bytes = c->q * c->n * c->rs;
   const int64_t k0 = c->kernels;
   for (int s = 0; s < S; ++s) {
     cudaEvent_t e = c->begin();
-    if (native) CUDA_TRY(cudaMemcpyAsync(c->seg_slot(s, 0), c->lattice(c->cur), lat_bytes, cudaMemcpyDeviceToDevice, c->ls));
-    else c->impl->encode(c->lattice(c->cur), s);
-    c->end(e, 3, 1, 0);
+    if (native || (moment && s == 0))
+      CUDA_TRY(cudaMemcpyAsync(c->seg_slot(s, 0), c->lattice(c->cur), lat_bytes, cudaMemcpyDeviceToDevice, c->ls));
+    else if (!moment) c->impl->encode(c->lattice(c->cur), s);
+    c->end(e, 3, moment && s > 0 ? 0 : 1, 0);
+    // moment checkpoints: the segment's last step also stores checkpoint s + 1
+    void* mom = moment && s + 1 < S ? c->ckpt_mom(s + 1) : nullptr;
     e = c->begin();
     if (c->use_flow) {   // the K steps of the segment in one persistent launch
-      c->impl->fwd_run(c->lattice(c->cur), c->lattice(c->cur ^ 1), 0, K, s * K, k.sample_every);
+      c->impl->fwd_run(c->lattice(c->cur), c->lattice(c->cur ^ 1), 0, K, s * K, k.sample_every, mom);
       c->cur ^= K & 1;
     } else {
       for (int j = 0; j < K; ++j) {
         const int step = s * K + j;
-        c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0);
+        c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0,
+                     j == K - 1 ? mom : nullptr);
         c->cur ^= 1;
       }
     }
@@ -813,10 +833,12 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
     c->fork_cur = rec ? c->rec_fork : c->fork_ev;
     c->join_cur = rec ? c->rec_join : c->join_ev;
   };
+  const bool moment = k.ckpt_format == LBM_CKPT_MOMENT;
   auto recompute = [&](int s) {
     cudaEvent_t e = c->begin();
-    if (!native) c->impl->decode(s, c->seg_slot(s, 0));
-    c->end(e, 3, native ? 0 : 1, 0);
+    const bool restore = !native && !(moment && s == 0);   // native slots are read in place
+    if (restore) c->impl->decode(s, c->seg_slot(s, 0));
+    c->end(e, 3, restore ? 1 : 0, 0);
     e = c->begin();
     if (flow) {
       if (K > 1) c->impl->fwd_run(c->seg_slot(s, 0), c->seg_slot(s, 1), lat, K - 1, 0, 0);

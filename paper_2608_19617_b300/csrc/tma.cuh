@@ -17,7 +17,8 @@
 // start left of x = 0 or end right of nx; those elements are filled with zero
 // and never used.  The node arithmetic is forward_core(), the same function
 // the per-step kernels use, and the block sums go to the same per-tile slots,
-// so results are bitwise those of fwd_interior_kernel.
+// so results agree with fwd_interior_kernel up to the compiler's choice of
+// fused multiply-adds in the two kernels.
 //
 // Every wait on a copy is bounded: a wait that runs out raises status[0],
 // waits (bounded) for the block's other copies in flight and leaves.
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kBlock) fwd_tma_kernel(const __grid_constant__
   R* buf = reinterpret_cast<R*>(tma_smem);
   pdl_enter();
   const Geo& g = A.geo;
-  const FwdStep<R> P{A.src, A.dst, A.sample};
+  const FwdStep<R> P{A.src, A.dst, A.sample, A.mom};
   const unsigned tid = threadIdx.x;
   if (tid == 0) {
     for (int s = 0; s < kTmaStages; ++s) mbar_init(&full[s], 1);

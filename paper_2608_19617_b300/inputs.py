@@ -31,7 +31,7 @@ OBJ_DISSIPATION, OBJ_VELOCITY_DEV, OBJ_PRESSURE, OBJ_DRAG = 0, 1, 2, 3
 # Monitored quantity of the window criterion (enum lbm_monitor_kind).
 MON_DRAG, MON_OBJECTIVE = 0, 1
 # Checkpoint storage (enum lbm_ckpt_format).
-CKPT_NATIVE, CKPT_FP16, CKPT_BF16 = 0, 1, 2
+CKPT_NATIVE, CKPT_FP16, CKPT_BF16, CKPT_MOMENT = 0, 1, 2, 3
 
 
 @dataclass

@@ -72,7 +72,7 @@ def _cfg(**kw):
 @pytest.mark.parametrize("field,value", [
     ("tau", 0.5), ("lattice", 7), ("nz", 0), ("window_len", 0), ("sample_every", 3),
     ("ckpt_every", 7), ("g_max", 1.5), ("precision", 5), ("rho_out", -1.0),
-    ("objective_kind", 9), ("q_interp", 0.0), ("ckpt_format", 3),
+    ("objective_kind", 9), ("q_interp", 0.0), ("ckpt_format", 4),
 ])
 def test_invalid_configs_are_rejected(lib, field, value):
     cfg = _cfg()
@@ -95,6 +95,24 @@ def test_sixteen_bit_checkpoints_need_fp32(lib):
     cfg.ckpt_format = 1
     with pytest.raises(B.LbmError):
         B.workspace_size(cfg)
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_moment_checkpoints_are_smaller_and_allowed_in_fp64(lib, lattice):
+    """Checkpoints 1..S-1 keep 6 (2D) / 10 (3D) coefficient planes instead of
+    Q; checkpoint 0 stays native.  The format is lossless, so FP64 may use it."""
+    case = I.small_channel(64, 12, window_len=40, ckpt_every=4) if lattice == 9 else \
+        I.small_duct3d(32, 8, 8, window_len=40, ckpt_every=4)
+    sizes = {}
+    for fmt in (I.CKPT_NATIVE, I.CKPT_MOMENT):
+        cfg = B.config_from_case(case.replace(ckpt_format=fmt))
+        sizes[fmt] = B.workspace_size(cfg)
+    n, S, R = case.n, 10, 4
+    saved = (S - 1) * (lattice - (6 if lattice == 9 else 10)) * n * R   # checkpoint planes saved
+    extra = n * R * lattice                                                # one more segment slot (K, not K-1)
+    assert sizes[I.CKPT_NATIVE] - sizes[I.CKPT_MOMENT] == pytest.approx(saved - extra, abs=4096 * 12)
+    cfg = B.config_from_case(case.replace(ckpt_format=I.CKPT_MOMENT), precision=B.LBM_FP64)
+    assert B.workspace_size(cfg) > 0
 
 
 def test_bad_box_rejected(lib):

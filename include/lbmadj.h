@@ -84,12 +84,14 @@ enum { LBM_MON_DRAG = 0, LBM_MON_OBJECTIVE = 1 };
  *        scale per block of nodes plus FP32 density and momentum (lossy; FP32
  *        solver only).
  *  MOMENT: lossless and smaller (a library design with no counterpart in the
- *        paper).  Every carried value is p~_a = w_a (A + B.c_a + c_a.T.c_a)
- *        with one scalar A, vector B and symmetric tensor T per node (the
- *        regularized collision and blend of Eqs. 16 and 23), so checkpoints
- *        1 .. S-1 keep those 6 (2D) or 10 (3D) values, stored by the step that
- *        produces the field, and regenerate it bitwise.  Checkpoint 0, the
- *        window's start field, which need not come from a step, stays native. */
+ *        paper).  Every carried value is p~_a = w_a (a0 + b m.c_a + 4.5
+ *        c_a.X.c_a), evaluated with fused multiply-adds in a fixed order,
+ *        from the node's a0, b, momentum m and symmetric X = m u^T + om Pi
+ *        (the regularized collision and blend of Eqs. 16 and 23).
+ *        Checkpoints 1 .. S-1 keep those 7 (2D) or 11 (3D) values, stored by
+ *        the step that produces the field, and regenerate it bitwise.
+ *        Checkpoint 0, the window's start field, which need not come from a
+ *        step, stays native. */
 enum { LBM_CKPT_NATIVE = 0, LBM_CKPT_FP16 = 1, LBM_CKPT_BF16 = 2, LBM_CKPT_MOMENT = 3 };
 
 typedef struct {
@@ -241,6 +243,22 @@ lbm_status lbm_set_graphs(lbm_ctx* ctx, int32_t enable);
  * so that each launch overlaps the tail of the previous one, or plainly (0).
  * Results are identical either way. */
 lbm_status lbm_set_pdl(lbm_ctx* ctx, int32_t enable);
+
+/* One window of ctx along the trajectory of ref: ctx runs its window as
+ * lbm_step_window does, except that each checkpoint segment s starts from
+ * ref's checkpoint s of ref's last window (decoded if 16-bit or moment,
+ * converted to ctx's precision).  ctx's checkpoints, window sums and the
+ * adjoint of a following lbm_adjoint_window(ctx) then follow ref's primal
+ * trajectory, up to ctx's own arithmetic within each segment.  This is the
+ * "same trajectory" comparison of an FP32 (or mixed-precision) adjoint with
+ * an FP64 one on a chaotic flow, where independent FP32 and FP64 runs over a
+ * long window drift apart.  Both contexts need the same lattice, window
+ * length and checkpoint interval, and ctx must not use moment checkpoints
+ * (its segments restart from ref's fields): LBM_ERR_ARG otherwise; ref needs
+ * a completed window (LBM_ERR_STATE).  ref's segment buffer serves as decode
+ * scratch, which a later lbm_adjoint_window(ref) overwrites anyway.
+ * Synchronises both streams; launched directly, not as a replayed graph. */
+lbm_status lbm_step_window_along(lbm_ctx* ctx, lbm_ctx* ref, double* J_window, double* monitor_window);
 
 /* Run each checkpoint segment of the forward window, of the recompute and of
  * the adjoint sweep as ONE persistent launch (1) instead of one launch per

@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
                             c_void_p, POINTER(c_void_p)]),
         "lbm_step_window": (st, [c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_window_converged": (st, [c_void_p, POINTER(c_int32), POINTER(c_double)]),
+        "lbm_step_window_along": (st, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_window_objectives": (st, [c_void_p, c_void_p, c_void_p, c_size_t]),
         "lbm_adjoint_window": (st, [c_void_p, POINTER(c_double)]),
         "lbm_design_gradient": (st, [c_void_p, c_void_p, c_size_t]),
@@ -190,6 +191,13 @@ class Solver:
     def step_window(self):
         j, m = c_double(), c_double()
         check(lib().lbm_step_window(self.ctx, byref(j), byref(m)), "lbm_step_window")
+        return j.value, m.value
+
+    def step_window_along(self, ref):
+        """One window along the trajectory of another solver's last window
+        (lbm_step_window_along): each segment starts from ref's checkpoint."""
+        j, m = c_double(), c_double()
+        check(lib().lbm_step_window_along(self.ctx, ref.ctx, byref(j), byref(m)), "lbm_step_window_along")
         return j.value, m.value
 
     def window_converged(self):

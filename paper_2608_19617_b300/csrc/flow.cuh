@@ -137,7 +137,8 @@ __device__ __noinline__ void fwd_face_node(const FwdArgs<R>& A, const FwdStep<R>
   const unsigned i = A.ft.idx[kf];
   int x, y, z;
   flow_coords(A.geo, i, x, y, z);
-  forward_node<L, R, true, true>(A, P, x, y, z, i, kf, bj, bm);
+  if (P.mom) forward_node<L, R, true, true, true>(A, P, x, y, z, i, kf, bj, bm);
+  else forward_node<L, R, true, true, false>(A, P, x, y, z, i, kf, bj, bm);
 }
 
 template <class L, class R>
@@ -168,7 +169,10 @@ __global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 
     int x = x0, y = y0, z = z0;
 #pragma unroll 1
     for (unsigned i = i0 + threadIdx.x; i < i1; i += kFlowBlock) {
-      if (!flow_is_face<L>(g, x, y, z)) forward_node<L, R, false, true>(A, P, x, y, z, i, 0u, bj, bm);
+      if (!flow_is_face<L>(g, x, y, z)) {
+        if (P.mom) forward_node<L, R, false, true, true>(A, P, x, y, z, i, 0u, bj, bm);
+        else forward_node<L, R, false, true, false>(A, P, x, y, z, i, 0u, bj, bm);
+      }
       flow_advance(g, x, y, z);
     }
 #pragma unroll 1

@@ -21,8 +21,8 @@
 // collision (Eq. 16) only carries Hermite moments up to second order, so
 // h_a = w_a (H0 + H1.c_a + c_a.H2.c_a), and the partial bounce-back of Eq. 23,
 // p = (1-g) h + g h_abar, keeps the even part and scales the odd part H1 by
-// (1 - 2g).  Hence p~_a = w_a (A + B.c_a + c_a.T.c_a) with one scalar, one
-// vector and one symmetric tensor per node; the adjoint of the blend scales
+// (1 - 2g).  Hence p~_a = w_a (a0 + b m.c_a + 4.5 c_a.X.c_a) with two scalars,
+// one vector and one symmetric tensor per node; the adjoint of the blend scales
 // the first adjoint moment by (1 - 2g); and the sensitivity term of Eq. 40,
 // sum_a a_a (h_abar - h_a), equals -6 m . sum_a w_a c_a a_a.
 //
@@ -291,6 +291,17 @@ __device__ __forceinline__ void raw_moments(const R (&f)[L::Q], R& m0, R (&m1)[3
   m2[0] = xx; m2[1] = yy; m2[2] = zz; m2[3] = xy; m2[4] = xz; m2[5] = yz;
 }
 
+// Explicitly rounded products and fused multiply-adds.  The per-node forward
+// arithmetic (moments, closure, blend, samples) is written with them, in a
+// fixed order, wherever a product meets a sum: the compiler then has no
+// contraction left to choose, and every kernel that inlines it (interior,
+// face, TMA-staged, persistent, the step that writes a moment checkpoint, the
+// checkpoint decoder) computes the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class L, class R>
 __device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<L, R>& M) {
   R rt, m[3], m2[6];
@@ -299,21 +310,22 @@ __device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, M
   M.rho = R(1) + rt;
   M.inv = R(1) / M.rho;
   M.m[0] = m[0]; M.m[1] = m[1]; M.m[2] = L::D == 3 ? m[2] : R(0);
-  M.u[0] = m[0] * M.inv; M.u[1] = m[1] * M.inv; M.u[2] = M.m[2] * M.inv;
+  M.u[0] = mul_rn(m[0], M.inv); M.u[1] = mul_rn(m[1], M.inv); M.u[2] = mul_rn(M.m[2], M.inv);
   // Pi = M2 - rho cs^2 I - m m^T / rho; with shifted moments M2~ = M2 - cs^2 I.
   const R c = cs2<R>();
-  M.pi[0] = m2[0] - rt * c - m[0] * M.u[0];
-  M.pi[1] = m2[1] - rt * c - m[1] * M.u[1];
-  M.pi[2] = (L::D == 3) ? m2[2] - rt * c - M.m[2] * M.u[2] : R(0);
-  M.pi[3] = m2[3] - m[0] * M.u[1];
-  M.pi[4] = (L::D == 3) ? m2[4] - m[0] * M.u[2] : R(0);
-  M.pi[5] = (L::D == 3) ? m2[5] - m[1] * M.u[2] : R(0);
-  M.pp = M.pi[0] * M.pi[0] + M.pi[1] * M.pi[1] + M.pi[2] * M.pi[2] +
-         R(2) * (M.pi[3] * M.pi[3] + M.pi[4] * M.pi[4] + M.pi[5] * M.pi[5]);
-  M.pn = sqrt(R(2) * M.pp);
+  M.pi[0] = fma_rn(-m[0], M.u[0], fma_rn(-rt, c, m2[0]));
+  M.pi[1] = fma_rn(-m[1], M.u[1], fma_rn(-rt, c, m2[1]));
+  M.pi[2] = (L::D == 3) ? fma_rn(-M.m[2], M.u[2], fma_rn(-rt, c, m2[2])) : R(0);
+  M.pi[3] = fma_rn(-m[0], M.u[1], m2[3]);
+  M.pi[4] = (L::D == 3) ? fma_rn(-m[0], M.u[2], m2[4]) : R(0);
+  M.pi[5] = (L::D == 3) ? fma_rn(-m[1], M.u[2], m2[5]) : R(0);
+  const R diag = fma_rn(M.pi[2], M.pi[2], fma_rn(M.pi[1], M.pi[1], mul_rn(M.pi[0], M.pi[0])));
+  const R off = fma_rn(M.pi[5], M.pi[5], fma_rn(M.pi[4], M.pi[4], mul_rn(M.pi[3], M.pi[3])));
+  M.pp = fma_rn(R(2), off, diag);
+  M.pn = sqrt(mul_rn(R(2), M.pp));
   // Eq. 14: 2 C^2 |Pi| / (rho cs^4) = 18 C^2 |Pi| / rho.
-  M.s = sqrt(ph.tau * ph.tau + R(18) * ph.c2 * M.pn * M.inv);
-  M.te = R(0.5) * (ph.tau + M.s);
+  M.s = sqrt(fma_rn(mul_rn(mul_rn(R(18), ph.c2), M.pn), M.inv, mul_rn(ph.tau, ph.tau)));
+  M.te = mul_rn(R(0.5), ph.tau + M.s);
   M.om = R(1) - R(1) / M.te;
 }
 
@@ -337,29 +349,49 @@ __device__ __forceinline__ R quad_form(int a, R s0, const R (&s1)[3], const R (&
 
 // Blended post-collision field (Eqs. 16 and 23):
 //   h~_a = f^eq_a - w_a + (1 - 1/tau_eff) w_a/(2 cs^4) (c_a c_a - cs^2 I) : Pi
-//        = w_a (A + 3 m.c_a + c_a.T.c_a),
-//   A = rho - 1 - 1.5 m.u - 1.5 om tr(Pi),  T = 4.5 (m u^T + om Pi),
-// and the blend scales the odd part: p~_a = w_a (A + 3 (1 - 2g) m.c_a + c_a.T.c_a).
-//
-// B and T are formed with rounded multiplies that the compiler may not fuse
-// into the additions of quad_form: the coefficients a step adds are then
-// exactly the rounded values a moment checkpoint stores.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+//        = w_a (a0 + 3 m.c_a + 4.5 c_a.X.c_a),
+//   a0 = rho - 1 - 1.5 m.u - 1.5 om tr(Pi),  X = m u^T + om Pi,
+// and the blend scales the odd part: p~_a = w_a (a0 + b m.c_a + 4.5 c_a.X.c_a)
+// with b = 3 (1 - 2g).  Two scalars a0, b, the vector m and the symmetric X
+// per node give every direction.
+template <class R>
+struct Blend {
+  R a0, b;
+  R m[3];
+  R X[6];   // xx, yy, zz, xy, xz, yz
+};
 
 template <class L, class R>
-__device__ __forceinline__ void post_collision(const Mom<L, R>& M, R g, R& A, R (&B)[3], R (&T)[6]) {
+__device__ __forceinline__ void blend_coefs(const Mom<L, R>& M, R g, Blend<R>& C) {
   const R tr = M.pi[0] + M.pi[1] + M.pi[2];
-  A = M.rt - R(1.5) * (M.m[0] * M.u[0] + M.m[1] * M.u[1] + M.m[2] * M.u[2]) - R(1.5) * M.om * tr;
-  const R b = R(3) * (R(1) - R(2) * g);
-  B[0] = mul_rn(b, M.m[0]); B[1] = mul_rn(b, M.m[1]); B[2] = mul_rn(b, M.m[2]);
-  const R k = R(4.5);
-  T[0] = mul_rn(k, M.m[0] * M.u[0] + M.om * M.pi[0]);
-  T[1] = mul_rn(k, M.m[1] * M.u[1] + M.om * M.pi[1]);
-  T[2] = mul_rn(k, M.m[2] * M.u[2] + M.om * M.pi[2]);
-  T[3] = mul_rn(k, M.m[0] * M.u[1] + M.om * M.pi[3]);
-  T[4] = mul_rn(k, M.m[0] * M.u[2] + M.om * M.pi[4]);
-  T[5] = mul_rn(k, M.m[1] * M.u[2] + M.om * M.pi[5]);
+  const R mu = fma_rn(M.m[2], M.u[2], fma_rn(M.m[1], M.u[1], mul_rn(M.m[0], M.u[0])));
+  C.a0 = fma_rn(mul_rn(R(-1.5), M.om), tr, fma_rn(R(-1.5), mu, M.rt));
+  C.b = mul_rn(R(3), fma_rn(R(-2), g, R(1)));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) C.m[k] = M.m[k];
+  C.X[0] = fma_rn(M.om, M.pi[0], mul_rn(M.m[0], M.u[0]));
+  C.X[1] = fma_rn(M.om, M.pi[1], mul_rn(M.m[1], M.u[1]));
+  C.X[2] = fma_rn(M.om, M.pi[2], mul_rn(M.m[2], M.u[2]));
+  C.X[3] = fma_rn(M.om, M.pi[3], mul_rn(M.m[0], M.u[1]));
+  C.X[4] = fma_rn(M.om, M.pi[4], mul_rn(M.m[0], M.u[2]));
+  C.X[5] = fma_rn(M.om, M.pi[5], mul_rn(M.m[1], M.u[2]));
+}
+
+// p~_a / w_a from the blend coefficients, fused multiply-adds in a fixed order.
+template <class L, class R>
+__device__ __forceinline__ R blend_value(int a, const Blend<R>& C) {
+  const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+  R v = C.a0;
+  if (cx) v = fma_rn(cx > 0 ? C.b : -C.b, C.m[0], v);
+  if (cy) v = fma_rn(cy > 0 ? C.b : -C.b, C.m[1], v);
+  if (cz) v = fma_rn(cz > 0 ? C.b : -C.b, C.m[2], v);
+  if (cx) v = fma_rn(R(4.5), C.X[0], v);
+  if (cy) v = fma_rn(R(4.5), C.X[1], v);
+  if (cz) v = fma_rn(R(4.5), C.X[2], v);
+  if (cx * cy) v = fma_rn(cx * cy > 0 ? R(9) : R(-9), C.X[3], v);
+  if (cx * cz) v = fma_rn(cx * cz > 0 ? R(9) : R(-9), C.X[4], v);
+  if (cy * cz) v = fma_rn(cy * cz > 0 ? R(9) : R(-9), C.X[5], v);
+  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -424,13 +456,15 @@ struct FwdArgs {
 template <class L, class R>
 __device__ __forceinline__ R local_objective(const Mom<L, R>& M, const Obj<R>& ob, R gi) {
   switch (ob.kind) {
-    case OBJ_DISS: return R(1.5) * (M.te - R(0.5)) * M.pp * M.inv / (M.te * M.te);
+    case OBJ_DISS:
+      return mul_rn(mul_rn(mul_rn(R(1.5), M.te - R(0.5)), M.pp), M.inv) / mul_rn(M.te, M.te);
     case OBJ_VEL: {
       const R dx = M.u[0] - ob.uref[0], dy = M.u[1] - ob.uref[1], dz = M.u[2] - ob.uref[2];
-      return dx * dx + dy * dy + (L::D == 3 ? dz * dz : R(0));
+      const R v = fma_rn(dy, dy, mul_rn(dx, dx));
+      return L::D == 3 ? fma_rn(dz, dz, v) : v;
     }
-    case OBJ_PRES: return cs2<R>() * M.rt;     // constant cs^2 sum(w) added at the window end
-    default: return R(-2) * gi * M.m[0];       // sum_a c_xa F_a = -2 g m_x
+    case OBJ_PRES: return mul_rn(cs2<R>(), M.rt);   // constant cs^2 sum(w) added at the window end
+    default: return mul_rn(mul_rn(R(-2), gi), M.m[0]);   // sum_a c_xa F_a = -2 g m_x
   }
 }
 
@@ -451,34 +485,58 @@ struct FwdStep {
   R* mom;         // non-null: moment checkpoint of p^n (mom_coefs<L>() planes of n values)
 };
 
-// Moment checkpoints.  The carried field is p~_a = w_a (A + B.c_a + c_a.T.c_a)
-// at every node (interior and face alike), so the FP32 (or FP64) values of A,
-// B and T as the step computed them regenerate p~ exactly: 1 + D + D(D+1)/2
-// planes (6 in 2D, 10 in 3D) instead of Q.
+// Moment checkpoints.  The carried field is p~_a = w_a blend_value(a, C) at
+// every node (interior and face alike), so the coefficients C as the step
+// computed them regenerate p~ exactly: a0, b, m (D values) and X (D(D+1)/2),
+// 7 planes in 2D and 11 in 3D instead of Q.
 template <class L>
-__host__ __device__ constexpr int mom_coefs() { return L::D == 2 ? 6 : 10; }
+__host__ __device__ constexpr int mom_coefs() { return L::D == 2 ? 7 : 11; }
 
 template <class L, class R>
-__device__ __forceinline__ void store_coefs(R* mom, unsigned n, unsigned i, R a0, const R (&B)[3], const R (&T)[6]) {
-  mom[i] = a0;
+__device__ __forceinline__ void store_coefs(R* mom, unsigned n, unsigned i, const Blend<R>& C) {
+  mom[i] = C.a0;
+  mom[n + i] = C.b;
   if (L::D == 2) {
-    mom[n + i] = B[0];
-    mom[2 * n + i] = B[1];
-    mom[3 * n + i] = T[0];
-    mom[4 * n + i] = T[1];
-    mom[5 * n + i] = T[3];
+    mom[2 * n + i] = C.m[0];
+    mom[3 * n + i] = C.m[1];
+    mom[4 * n + i] = C.X[0];
+    mom[5 * n + i] = C.X[1];
+    mom[6 * n + i] = C.X[3];
   } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) mom[(1 + k) * n + i] = B[k];
+    for (int k = 0; k < 3; ++k) mom[(2 + k) * n + i] = C.m[k];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) mom[(4 + k) * n + i] = T[k];
+    for (int k = 0; k < 6; ++k) mom[(5 + k) * n + i] = C.X[k];
+  }
+}
+
+template <class L, class R>
+__device__ __forceinline__ void load_coefs(const R* __restrict__ mom, unsigned n, unsigned i, Blend<R>& C) {
+  C.a0 = mom[i];
+  C.b = mom[n + i];
+  C.m[2] = R(0);
+  C.X[2] = C.X[4] = C.X[5] = R(0);
+  if (L::D == 2) {
+    C.m[0] = mom[2 * n + i];
+    C.m[1] = mom[3 * n + i];
+    C.X[0] = mom[4 * n + i];
+    C.X[1] = mom[5 * n + i];
+    C.X[3] = mom[6 * n + i];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C.m[k] = mom[(2 + k) * n + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) C.X[k] = mom[(5 + k) * n + i];
   }
 }
 
 // Collision, blend, store and sample of one node whose pulled populations f
 // are loaded (Eqs. 12-16, 23, 24-25); a sampled step adds the node's
-// objective and monitor terms to bj, bm.
-template <class L, class R>
+// objective and monitor terms to bj, bm.  MOM: the step also stores its blend
+// coefficients to P.mom (a moment checkpoint).  That step runs its own kernel
+// instantiation, so the other steps carry no branch for it; the explicit
+// arithmetic makes both instantiations compute the same bits.
+template <class L, class R, bool MOM = false>
 __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<R>& P, int x, int y, int z,
                                              unsigned i, const R (&f)[L::Q], R& bj, R& bm) {
   const Geo& g = A.geo;
@@ -486,19 +544,19 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
   moments<L, R>(f, A.ph, M);
   if (!(M.rho > R(0)) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
   const R gi = A.gfield[i];
-  R a0, B[3], T[6];
-  post_collision<L, R>(M, gi, a0, B, T);
-  if (P.mom) store_coefs<L, R>(P.mom, g.n, i, a0, B, T);
+  Blend<R> C;
+  blend_coefs<L, R>(M, gi, C);
+  if constexpr (MOM) store_coefs<L, R>(P.mom, g.n, i, C);
   R* dst = P.dst;
 #pragma unroll
-  for (int a = 0; a < L::Q; ++a) dst[a * g.n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
+  for (int a = 0; a < L::Q; ++a) dst[a * g.n + i] = mul_rn(R(L::w(a)), blend_value<L, R>(a, C));
   if (P.sample) {
     const int* b = A.obj.box;
     if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
       const R w = R(A.wobj[i]);
-      if (w != R(0)) bj += w * local_objective<L, R>(M, A.obj, gi);
+      if (w != R(0)) bj = fma_rn(w, local_objective<L, R>(M, A.obj, gi), bj);
     }
-    if (A.obj.mon == MON_DRAG) bm += R(-2) * gi * M.m[0];
+    if (A.obj.mon == MON_DRAG) bm = fma_rn(mul_rn(R(-2), gi), M.m[0], bm);
   }
 }
 
@@ -506,7 +564,7 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
 // the boundary populations of a face node (Eqs. 19-21), then forward_core.
 // For a face node k is its row in the face table; for an interior node k is unused.
 // CG: the source field is written concurrently by other blocks of the launch.
-template <class L, class R, bool FACE, bool CG = false>
+template <class L, class R, bool FACE, bool CG = false, bool MOM = false>
 __device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<R>& P, int x, int y, int z,
                                              unsigned i, unsigned k, R& bj, R& bm) {
   const Geo& g = A.geo;
@@ -522,12 +580,12 @@ __device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) f[a] = ldf<CG>(src + (a * g.n + i - offset<L>(g, a)));
   }
-  forward_core<L, R>(A, P, x, y, z, i, f, bj, bm);
+  forward_core<L, R, MOM>(A, P, x, y, z, i, f, bj, bm);
 }
 
 // Interior nodes: x in [1, nx-1), y in [1, ny-1), z in [1, nz-1) (3D).  No
 // face logic at all, so the instruction stream stays short.
-template <class L, class R>
+template <class L, class R, bool MOM = false>
 __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
@@ -535,7 +593,7 @@ __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
   const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
   R bj = 0, bm = 0;
   if (x < g.nx - 1)
-    forward_node<L, R, false>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
+    forward_node<L, R, false, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
   if (A.sample) {   // uniform across the grid
     block_sum2<R>(bj, bm);
     sample_commit(double(bj), double(bm), A.blk);
@@ -543,7 +601,7 @@ __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
 }
 
 // Face nodes, from the list face[0..nface); block sums after the interior's.
-template <class L, class R>
+template <class L, class R, bool MOM = false>
 __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned blk0) {
   pdl_enter();
   const Geo& g = A.geo;
@@ -552,7 +610,7 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   const unsigned i = k < A.ft.n ? A.ft.idx[k] : kNone;   // rows padded per slice hold kNone
   if (i != kNone) {
     const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
-    forward_node<L, R, true>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, k, bj, bm);
+    forward_node<L, R, true, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, k, bj, bm);
   }
   if (A.sample) {
     block_sum2<R>(bj, bm);
@@ -1012,28 +1070,16 @@ __global__ void gradient_kernel(const double2* __restrict__ gacc, const float* _
   }
 }
 
-// Moment checkpoint -> p~ at every node: w_a (A + B.c_a + c_a.T.c_a) with the
-// same expression as the step kernels, so the field is bitwise the one stored.
+// Moment checkpoint -> p~ at every node: w_a blend_value(a, C), the step
+// kernels' own arithmetic, so the field is bitwise the one the step stored.
 template <class L, class R>
 __global__ void __launch_bounds__(kBlock) mom_decode_kernel(const R* __restrict__ mom, R* __restrict__ p, unsigned n) {
   const unsigned i = blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
-  R B[3] = {R(0), R(0), R(0)}, T[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-  const R a0 = mom[i];
-  if (L::D == 2) {
-    B[0] = mom[n + i];
-    B[1] = mom[2 * n + i];
-    T[0] = mom[3 * n + i];
-    T[1] = mom[4 * n + i];
-    T[3] = mom[5 * n + i];
-  } else {
+  Blend<R> C;
+  load_coefs<L, R>(mom, n, i, C);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) B[k] = mom[(1 + k) * n + i];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) T[k] = mom[(4 + k) * n + i];
-  }
-#pragma unroll
-  for (int a = 0; a < L::Q; ++a) p[a * n + i] = R(L::w(a)) * quad_form<L, R>(a, a0, B, T);
+  for (int a = 0; a < L::Q; ++a) p[a * n + i] = mul_rn(R(L::w(a)), blend_value<L, R>(a, C));
 }
 
 template <class L, class R>
@@ -1062,6 +1108,14 @@ __global__ void shift_kernel(const double* __restrict__ src, R* __restrict__ dst
     if (!isfinite(v)) *bad = 1;
     dst[k] = R(v - w);
   }
+}
+
+// Shifted field of one working precision into another (same [Q][N] layout).
+template <class S, class D>
+__global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, long long total) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x)
+    dst[k] = D(src[k]);
 }
 
 template <class R>

@@ -164,7 +164,7 @@ Layout make_layout(const lbm_config& c) {
   const bool moment = c.ckpt_format == LBM_CKPT_MOMENT;
   // moment checkpoints: slot 0 (the window's start field) native, slots 1.. the coefficient planes
   L.ckpt_slot = native   ? lat
-                : moment ? align_up(size_t(d == 2 ? 6 : 10) * n * rs)
+                : moment ? align_up(size_t(d == 2 ? 7 : 11) * n * rs)
                          : align_up(size_t(q) * n * 2) + align_up(size_t(d + 1) * n * 4) +
                                align_up(size_t(L.nblocks_1d) * 4);
   L.seg_slots = native ? size_t(c.ckpt_every - 1) : size_t(c.ckpt_every);
@@ -242,6 +242,10 @@ struct Impl {
   virtual void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
                        int nsteps, int step0) = 0;
   virtual bool tma_setup() = 0;      // encoder and launch shape of the TMA-staged kernels
+  // Field of checkpoint s of the last window (decoded if need be), in this context's precision.
+  virtual const void* checkpoint_field(int s) = 0;
+  // dst (this context's precision) <- src field in precision rs_src.
+  virtual void import_field(const void* src, size_t rs_src, void* dst) = 0;
 };
 
 // A captured CUDA graph with the timing events its replays record.
@@ -275,6 +279,7 @@ struct lbm_ctx {
   int flow_silent = -1;       // test hook: a band that never publishes
   int64_t kernels = 0;        // kernel launches enqueued so far
   int64_t kernels_window = 0, kernels_adjoint = 0;   // per window / per adjoint sweep, as last enqueued
+  lbm_ctx* along = nullptr;   // lbm_step_window_along: the context whose checkpoints start each segment
   bool capturing = false;
   std::vector<Pending>* sink = nullptr;   // where end() files events while capturing
   GraphRec gwin[2][2];        // forward window graphs by [start parity][timing]
@@ -497,13 +502,20 @@ struct ImplT final : Impl {
     const lbm::FwdArgs<R> A = fwd_args(src, dst, sample, mom);
     const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
     const CUtensorMap* map = c->use_tma ? tensor_map(src) : nullptr;
+    // the step that writes a moment checkpoint runs its own instantiation (MOM)
     fork_join(
         [&](cudaStream_t st) {
-          if (map) launch_tma(lbm::fwd_tma_kernel<L, R>, st, *map, A, blk0, unsigned(c->lay.igx),
-                              unsigned(c->lay.igy), c->template at<int>(c->lay.flags) + 2);
-          else launch(lbm::fwd_interior_kernel<L, R>, igrid(), st, A);
+          int* status = c->template at<int>(c->lay.flags) + 2;
+          const unsigned gx = unsigned(c->lay.igx), gy = unsigned(c->lay.igy);
+          if (map && mom) launch_tma(lbm::fwd_tma_kernel<L, R, true>, st, *map, A, blk0, gx, gy, status);
+          else if (map) launch_tma(lbm::fwd_tma_kernel<L, R, false>, st, *map, A, blk0, gx, gy, status);
+          else if (mom) launch(lbm::fwd_interior_kernel<L, R, true>, igrid(), st, A);
+          else launch(lbm::fwd_interior_kernel<L, R, false>, igrid(), st, A);
         },
-        [&](cudaStream_t st) { launch(lbm::fwd_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A, blk0); });
+        [&](cudaStream_t st) {
+          if (mom) launch(lbm::fwd_face_kernel<L, R, true>, dim3(c->lay.face_blocks), st, A, blk0);
+          else launch(lbm::fwd_face_kernel<L, R, false>, dim3(c->lay.face_blocks), st, A, blk0);
+        });
   }
 
   // TMA-staged interior kernels (tma.cuh).
@@ -523,10 +535,11 @@ struct ImplT final : Impl {
     encode_map = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     const size_t smem = lbm::fwd_tma_smem<L, R>();
     int dev = 0, sms = 0, per_sm = 0;
-    if (cudaFuncSetAttribute(lbm::fwd_tma_kernel<L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
+    if (cudaFuncSetAttribute(lbm::fwd_tma_kernel<L, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
+        cudaFuncSetAttribute(lbm::fwd_tma_kernel<L, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
         cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::fwd_tma_kernel<L, R>, lbm::kBlock, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::fwd_tma_kernel<L, R, true>, lbm::kBlock, smem) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       return false;
@@ -571,6 +584,23 @@ struct ImplT final : Impl {
     const lbm::AdjArgs<R> A = adj_args(bnext, pprev, bout, sample);
     fork_join([&](cudaStream_t st) { launch(lbm::adj_interior_kernel<L, R>, igrid(), st, A); },
               [&](cudaStream_t st) { launch(lbm::adj_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A); });
+  }
+
+  const void* checkpoint_field(int s) override {
+    const int fmt = c->cfg.ckpt_format;
+    if (fmt == LBM_CKPT_NATIVE || (fmt == LBM_CKPT_MOMENT && s == 0)) return c->seg_slot(s, 0);
+    decode(s, c->seg_slot(s, 0));
+    return c->seg_slot(s, 0);
+  }
+  void import_field(const void* src, size_t rs_src, void* dst) override {
+    const long long total = (long long)(c->n * c->q);
+    c->kernels += 1;
+    if (rs_src == 4)
+      lbm::convert_kernel<float, R><<<flat_blocks(), 256, 0, c->ls>>>(static_cast<const float*>(src),
+                                                                       static_cast<R*>(dst), total);
+    else
+      lbm::convert_kernel<double, R><<<flat_blocks(), 256, 0, c->ls>>>(static_cast<const double*>(src),
+                                                                        static_cast<R*>(dst), total);
   }
 
   // Persistent step kernels.
@@ -771,6 +801,14 @@ lbm_status enqueue_window(lbm_ctx* c) {
   const size_t lat_bytes = c->q * c->n * c->rs;
   const int64_t k0 = c->kernels;
   for (int s = 0; s < S; ++s) {
+    if (c->along) {   // start the segment from the reference context's checkpoint s
+      lbm_ctx* r = c->along;
+      cudaStream_t rls = r->ls;
+      r->ls = c->ls;
+      const void* src = r->impl->checkpoint_field(s);
+      r->ls = rls;
+      c->impl->import_field(src, r->rs, c->lattice(c->cur));
+    }
     cudaEvent_t e = c->begin();
     if (native || (moment && s == 0))
       CUDA_TRY(cudaMemcpyAsync(c->seg_slot(s, 0), c->lattice(c->cur), lat_bytes, cudaMemcpyDeviceToDevice, c->ls));
@@ -1290,6 +1328,47 @@ lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window)
     c->grad_valid = false;
     return fail(LBM_ERR_NONFINITE, "window %lld produced a non-positive density or a non-finite value",
                 (long long)c->windows);
+  }
+  c->windows += 1;
+  c->window_valid = true;
+  c->grad_valid = false;
+  c->last_j = acc.jmean;
+  c->last_m = acc.mmean;
+  c->nwin_for_ratio += 1;
+  c->ratio = c->nwin_for_ratio >= 2 ? acc.ratio : INFINITY;
+  c->converged = c->nwin_for_ratio >= 2 ? acc.converged : 0;
+  if (J_window) *J_window = acc.jmean;
+  if (monitor_window) *monitor_window = acc.mmean;
+  return LBM_OK;
+}
+
+lbm_status lbm_step_window_along(lbm_ctx* c, lbm_ctx* ref, double* J_window, double* monitor_window) {
+  if (!c || !ref) return fail(LBM_ERR_ARG, "null context");
+  if (c == ref) return fail(LBM_ERR_ARG, "the reference must be another context");
+  const lbm_config &k = c->cfg, &r = ref->cfg;
+  if (k.lattice != r.lattice || k.nx != r.nx || k.ny != r.ny || k.nz != r.nz || k.window_len != r.window_len ||
+      k.ckpt_every != r.ckpt_every)
+    return fail(LBM_ERR_ARG, "the reference must have the same lattice, window length and checkpoint interval");
+  if (k.ckpt_format == LBM_CKPT_MOMENT)
+    return fail(LBM_ERR_ARG, "a window along a reference cannot store moment checkpoints (its segments restart)");
+  if (!ref->window_valid) return fail(LBM_ERR_STATE, "the reference has no completed window");
+  CUDA_TRY(cudaStreamSynchronize(ref->stream));
+  // one direct enqueue: no graph holds the reference's buffers
+  c->along = ref;
+  const lbm_status st = enqueue_window(c);
+  c->along = nullptr;
+  LBM_TRY(st);
+  CUDA_TRY(cudaGetLastError());
+  lbm::WindowAcc acc;
+  CUDA_TRY(cudaMemcpyAsync(&acc, c->at(c->lay.acc), sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->harvest();
+  c->steps += k.window_len;
+  if (acc.stalled || acc.nonfinite) {
+    CUDA_TRY(cudaMemsetAsync(c->at<int>(c->lay.flags) + 2, 0, sizeof(int), c->stream));
+    c->window_valid = false;
+    c->grad_valid = false;
+    return fail(acc.stalled ? LBM_ERR_CUDA : LBM_ERR_NONFINITE, "the window along the reference failed");
   }
   c->windows += 1;
   c->window_valid = true;

@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(lbm::kBlock) fwd_step_noalloc_kernel(lbm::FwdA
     if (!(M.rho > 0.f) || !isfinite(M.pn) || !isfinite(M.m[0] + M.m[1] + M.m[2])) *A.nonfinite = 1;
     const double phi = 1.0 - double(gamma[i]);
     const float gi = float(g_max * (1.0 - phi * (1.0 + q) / (phi + q)));
-    float a0, B[3], T[6];
-    post_collision<L, float>(M, gi, a0, B, T);
+    Blend<float> C;
+    blend_coefs<L, float>(M, gi, C);
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = float(L::w(a)) * quad_form<L, float>(a, a0, B, T);
+    for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = mul_rn(float(L::w(a)), blend_value<L, float>(a, C));
     if (A.sample) {
       const int* b = A.obj.box;
       if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {

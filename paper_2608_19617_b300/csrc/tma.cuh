@@ -15,10 +15,9 @@
 // starting at x0 - 5 (a multiple of 4, as the TMA unit requires of the
 // innermost coordinate of a 4-byte type) covers every shift.  The box may
 // start left of x = 0 or end right of nx; those elements are filled with zero
-// and never used.  The node arithmetic is forward_core(), the same function
-// the per-step kernels use, and the block sums go to the same per-tile slots,
-// so results agree with fwd_interior_kernel up to the compiler's choice of
-// fused multiply-adds in the two kernels.
+// and never used.  The node arithmetic is forward_core(), the same explicitly
+// rounded function the per-step kernels use, and the block sums go to the
+// same per-tile slots.
 //
 // Every wait on a copy is bounded: a wait that runs out raises status[0],
 // waits (bounded) for the block's other copies in flight and leaves.
@@ -96,7 +95,7 @@ __device__ __forceinline__ void tile_origin(unsigned t, unsigned igx, unsigned i
 
 // Interior forward step, TMA-staged.  Dynamic shared memory: kTmaStages x Q
 // rows of tma_row<R>() elements (fwd_tma_smem).
-template <class L, class R>
+template <class L, class R, bool MOM = false>
 __global__ void __launch_bounds__(kBlock) fwd_tma_kernel(const __grid_constant__ CUtensorMap src_map, FwdArgs<R> A,
                                                          unsigned ntiles, unsigned igx, unsigned igy, int* status) {
   extern __shared__ __align__(128) unsigned char tma_smem[];
@@ -150,7 +149,7 @@ __global__ void __launch_bounds__(kBlock) fwd_tma_kernel(const __grid_constant__
       R f[L::Q];
 #pragma unroll
       for (int a = 0; a < L::Q; ++a) f[a] = row[a * tma_row<R>() - L::cx(a)];
-      forward_core<L, R>(A, P, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, f, bj, bm);
+      forward_core<L, R, MOM>(A, P, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, f, bj, bm);
     }
     if (A.sample) {   // uniform across the grid
       block_sum2<R>(bj, bm);

@@ -99,7 +99,7 @@ def test_sixteen_bit_checkpoints_need_fp32(lib):
 
 @pytest.mark.parametrize("lattice", [9, 19])
 def test_moment_checkpoints_are_smaller_and_allowed_in_fp64(lib, lattice):
-    """Checkpoints 1..S-1 keep 6 (2D) / 10 (3D) coefficient planes instead of
+    """Checkpoints 1..S-1 keep 7 (2D) / 11 (3D) coefficient planes instead of
     Q; checkpoint 0 stays native.  The format is lossless, so FP64 may use it."""
     case = I.small_channel(64, 12, window_len=40, ckpt_every=4) if lattice == 9 else \
         I.small_duct3d(32, 8, 8, window_len=40, ckpt_every=4)
@@ -108,7 +108,7 @@ def test_moment_checkpoints_are_smaller_and_allowed_in_fp64(lib, lattice):
         cfg = B.config_from_case(case.replace(ckpt_format=fmt))
         sizes[fmt] = B.workspace_size(cfg)
     n, S, R = case.n, 10, 4
-    saved = (S - 1) * (lattice - (6 if lattice == 9 else 10)) * n * R   # checkpoint planes saved
+    saved = (S - 1) * (lattice - (7 if lattice == 9 else 11)) * n * R   # checkpoint planes saved
     extra = n * R * lattice                                                # one more segment slot (K, not K-1)
     assert sizes[I.CKPT_NATIVE] - sizes[I.CKPT_MOMENT] == pytest.approx(saved - extra, abs=4096 * 12)
     cfg = B.config_from_case(case.replace(ckpt_format=I.CKPT_MOMENT), precision=B.LBM_FP64)

@@ -1,10 +1,10 @@
 """Moment checkpoints (LBM_CKPT_MOMENT) are lossless.
 
-A moment checkpoint keeps the per-node collision coefficients (A, B, T) that
+A moment checkpoint keeps the per-node blend coefficients (a0, b, m, X) that
 the step producing the field computed; decoding applies the step's own
-expression w_a (A + B.c_a + c_a.T.c_a).  So the recomputed segments, the
-adjoint sweep and the gradient must be bitwise those of native checkpoints,
-on every launch path.
+arithmetic, w_a (a0 + b m.c_a + 4.5 c_a.X.c_a) with fused multiply-adds in a
+fixed order.  So the recomputed segments, the adjoint sweep and the gradient
+must be bitwise those of native checkpoints, on every launch path.
 """
 import numpy as np
 import pytest

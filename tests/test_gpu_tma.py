@@ -97,10 +97,20 @@ def test_tma_staging_matches_the_register_path(name):
 
 @pytest.mark.parametrize("fmt", [I.CKPT_FP16, I.CKPT_BF16])
 def test_tma_staging_with_sixteen_bit_checkpoints_and_pipeline(fmt):
+    """Forward states agree to rounding.  A last-place difference can move one
+    16-bit checkpoint value by a quantisation step, so the recomputed segments,
+    the adjoint and the gradient agree to the 16-bit format's resolution."""
     case = f32_inputs(I.small_channel(132, 12, window_len=24, ckpt_every=4, ckpt_format=fmt,
                                       outlet=I.OUTLET_P, tau=0.53))
     p0 = _start(case)
-    _same(_run(case, B.LBM_FP32, True, p0, pipeline=1), _run(case, B.LBM_FP32, False, p0, pipeline=1))
+    a = _run(case, B.LBM_FP32, True, p0, pipeline=1)
+    b = _run(case, B.LBM_FP32, False, p0, pipeline=1)
+    eps = 64 * 2.0 ** -23
+    for (ja, ma), (jb, mb) in zip(a["rec"], b["rec"]):
+        assert ja == pytest.approx(jb, rel=eps) and ma == pytest.approx(mb, rel=eps)
+    assert float(np.abs(a["state"] - b["state"]).max()) <= eps * float(np.abs(b["state"]).max())
+    for k in ("a0", "grad"):
+        assert np.linalg.norm(a[k] - b[k]) <= 1e-3 * np.linalg.norm(b[k]), k
 
 
 def test_tma_staging_of_a_batch():

@@ -266,9 +266,9 @@ lbm_status lbm_step_window_along(lbm_ctx* ctx, lbm_ctx* ref, double* J_window, d
  * counterpart in the paper) cut the lattice into bands of consecutive nodes,
  * one block per band, all blocks co-resident (cooperative launch); a block
  * starts step k once the bands its step reads from or writes over have
- * finished step k-1.  Nodes are computed by the same arithmetic as in the
- * per-step kernels (compiled in another context: results agree to a few
- * units in the last place); window sums are added in another order.
+ * finished step k-1.  Nodes are computed by the same explicitly rounded
+ * arithmetic as in the per-step kernels, so states, adjoint fields and
+ * gradients are theirs; window sums are added in another order.
  * The adjoint sweep then runs serially (cfg.pipeline is ignored).  Every wait
  * is bounded (4 s without progress): a wait that runs out makes the window or
  * sweep fail with LBM_ERR_CUDA instead of hanging.  Fails with LBM_ERR_ARG
@@ -279,9 +279,9 @@ lbm_status lbm_set_flow(lbm_ctx* ctx, int32_t enable);
 /* Stage the source rows of the interior forward steps (window and recompute)
  * in shared memory with TMA bulk-tensor copies, several tiles ahead of the
  * tile being computed (1), or load them straight into registers (0, the
- * default).  The node arithmetic and the block sums are the same code, so
- * results agree to a few units in the last place (the compiler may fuse
- * multiply-adds differently in the two kernels).  Needs interior nodes and a row pitch
+ * default).  The node arithmetic is the same explicitly rounded code and the
+ * block sums land in the same slots, so results are those of the register
+ * path.  Needs interior nodes and a row pitch
  * (nx * element size) that is a multiple of 16 bytes: LBM_ERR_ARG otherwise.
  * Copy waits are bounded; one that runs out fails the window or sweep with
  * LBM_ERR_CUDA. */

@@ -114,6 +114,18 @@ __device__ __forceinline__ bool neighbour(const Geo& g, int x, int y, int z, int
   return true;
 }
 
+// Explicitly rounded products and fused multiply-adds.  The per-node forward
+// arithmetic (boundary rules, moments, closure, blend,
+// samples) is written with them, in a
+// fixed order, wherever a product meets a sum: the compiler then has no
+// contraction left to choose, and every kernel that inlines it (interior,
+// face, TMA-staged, persistent, the step that writes a moment checkpoint, the
+// checkpoint decoder) computes the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class L>
 __device__ __forceinline__ bool on_face(const Geo& g, int x, int y, int z) {
   bool f = (x == 0) | (x == g.nx - 1) | (y == 0) | (y == g.ny - 1);
@@ -153,34 +165,38 @@ __device__ __forceinline__ void apply_rules(R (&f)[L::Q], unsigned mask, uint8_t
       if (mask & (1u << a)) f[a] = (mask & (1u << L::opp(a))) ? R(0) : f[L::opp(a)];
   } else if (cls == INLET) {
     if (L::Q == 9) {
-      const R s = f[0] + f[2] + f[4] + R(2) * (f[3] + f[6] + f[7]);
+      // Zou-He velocity inlet, Eq. 20, in shifted form (w1=w3, w5=w7, w2=w4).
+      const R s = fma_rn(R(2), f[3] + f[6] + f[7], f[0] + f[2] + f[4]);
       const R rho = (R(1) + s) / (R(1) - u0);
-      const R ru = rho * u0;
-      f[1] = f[3] + R(2.0 / 3.0) * ru;
-      f[5] = f[7] + R(0.5) * (f[4] - f[2]) + ru * R(1.0 / 6.0);
-      f[8] = f[6] + R(0.5) * (f[2] - f[4]) + ru * R(1.0 / 6.0);
+      const R ru = mul_rn(rho, u0);
+      f[1] = fma_rn(R(2.0 / 3.0), ru, f[3]);
+      f[5] = fma_rn(R(1.0 / 6.0), ru, fma_rn(R(0.5), f[4] - f[2], f[7]));
+      f[8] = fma_rn(R(1.0 / 6.0), ru, fma_rn(R(0.5), f[2] - f[4], f[6]));
     } else {
+      // Moving-wall bounce-back with rho0 = 1: f_a = f_abar + 2 w_a c_a.u / cs^2.
 #pragma unroll
       for (int a = 0; a < L::Q; ++a)
-        if (mask & (1u << a)) f[a] = f[L::opp(a)] + R(6.0 * L::w(a) * L::cx(a)) * u0;
+        if (mask & (1u << a)) f[a] = fma_rn(R(6.0 * L::w(a) * L::cx(a)), u0, f[L::opp(a)]);
     }
   } else if (cls == OUTLET_P) {
-    const R s = f[0] + f[2] + f[4] + R(2) * (f[1] + f[5] + f[8]);
+    // Zou-He pressure outlet, Eq. 21 (D2Q9): u = (1 + s)/rho0 - 1 in shifted form.
+    const R s = fma_rn(R(2), f[1] + f[5] + f[8], f[0] + f[2] + f[4]);
     const R ux = (R(1) + s) / rho_out - R(1);
-    const R ru = rho_out * ux;
-    f[3] = f[1] - R(2.0 / 3.0) * ru;
-    f[6] = f[8] + R(0.5) * (f[4] - f[2]) - ru * R(1.0 / 6.0);
-    f[7] = f[5] + R(0.5) * (f[2] - f[4]) - ru * R(1.0 / 6.0);
+    const R ru = mul_rn(rho_out, ux);
+    f[3] = fma_rn(R(-2.0 / 3.0), ru, f[1]);
+    f[6] = fma_rn(R(-1.0 / 6.0), ru, fma_rn(R(0.5), f[4] - f[2], f[8]));
+    f[7] = fma_rn(R(-1.0 / 6.0), ru, fma_rn(R(0.5), f[2] - f[4], f[5]));
   }
 }
 
 // ---------------------------------------------------------------------------
 // Streaming with boundary completion on a domain face: f^n at node (x,y,z)
-// from p^{n-1}.  Out of line: only face nodes come here.
+// from p^{n-1}, addresses from the geometry (no face table).  Returns the
+// mask of links that came from outside the domain.
 // ---------------------------------------------------------------------------
 template <class L, class R>
-__device__ __noinline__ unsigned gather_face(const R* __restrict__ P, const Geo& g, int x, int y, int z,
-                                             uint8_t cls, R u0, R rho_out, R* f) {
+__device__ __forceinline__ unsigned gather_geo(const R* __restrict__ P, const Geo& g, int x, int y, int z,
+                                               uint8_t cls, R u0, R rho_out, R (&f)[L::Q]) {
   unsigned unk = 0;
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
@@ -193,36 +209,7 @@ __device__ __noinline__ unsigned gather_face(const R* __restrict__ P, const Geo&
     }
   }
   if (!unk) return 0;
-  if (cls == WALL) {
-    // Eq. 19: an unknown population takes its opposite's value; a link whose
-    // opposite is unknown too stays at its rest weight (shifted value 0).
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a)
-      if (unk & (1u << a)) f[a] = (unk & (1u << L::opp(a))) ? R(0) : f[L::opp(a)];
-  } else if (cls == INLET) {
-    if (L::Q == 9) {
-      // Zou-He velocity inlet, Eq. 20, in shifted form (w1=w3, w5=w7, w2=w4).
-      const R s = f[0] + f[2] + f[4] + R(2) * (f[3] + f[6] + f[7]);
-      const R rho = (R(1) + s) / (R(1) - u0);
-      const R ru = rho * u0;
-      f[1] = f[3] + R(2.0 / 3.0) * ru;
-      f[5] = f[7] + R(0.5) * (f[4] - f[2]) + ru * R(1.0 / 6.0);
-      f[8] = f[6] + R(0.5) * (f[2] - f[4]) + ru * R(1.0 / 6.0);
-    } else {
-      // Moving-wall bounce-back with rho0 = 1: f_a = f_abar + 2 w_a c_a.u / cs^2.
-#pragma unroll
-      for (int a = 0; a < L::Q; ++a)
-        if (unk & (1u << a)) f[a] = f[L::opp(a)] + R(6.0 * L::w(a) * L::cx(a)) * u0;
-    }
-  } else if (cls == OUTLET_P) {
-    // Zou-He pressure outlet, Eq. 21 (D2Q9): u = (1 + s)/rho0 - 1 in shifted form.
-    const R s = f[0] + f[2] + f[4] + R(2) * (f[1] + f[5] + f[8]);
-    const R ux = (R(1) + s) / rho_out - R(1);
-    const R ru = rho_out * ux;
-    f[3] = f[1] - R(2.0 / 3.0) * ru;
-    f[6] = f[8] + R(0.5) * (f[4] - f[2]) - ru * R(1.0 / 6.0);
-    f[7] = f[5] + R(0.5) * (f[2] - f[4]) - ru * R(1.0 / 6.0);
-  } else if (cls == OUTLET_ZG) {
+  if (cls == OUTLET_ZG) {
     // Unknown f_a(i) = f_a(i + n_in) after streaming = p_a(i + n_in - c_a).
     const int xn = (x == g.nx - 1) ? x - 1 : x + 1;
 #pragma unroll
@@ -233,7 +220,20 @@ __device__ __noinline__ unsigned gather_face(const R* __restrict__ P, const Geo&
         f[a] = P[a * g.n + j];
       }
     }
+  } else {
+    apply_rules<L, R>(f, unk, cls, u0, rho_out);   // Eqs. 19-21
   }
+  return unk;
+}
+
+// Out-of-line copy for kernels whose face nodes are rare (no-allocation path).
+template <class L, class R>
+__device__ __noinline__ unsigned gather_face(const R* __restrict__ P, const Geo& g, int x, int y, int z,
+                                             uint8_t cls, R u0, R rho_out, R* f) {
+  R t[L::Q];
+  const unsigned unk = gather_geo<L, R>(P, g, x, y, z, cls, u0, rho_out, t);
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) f[a] = t[a];
   return unk;
 }
 
@@ -290,17 +290,6 @@ __device__ __forceinline__ void raw_moments(const R (&f)[L::Q], R& m0, R (&m1)[3
   m1[0] = mx; m1[1] = my; m1[2] = mz;
   m2[0] = xx; m2[1] = yy; m2[2] = zz; m2[3] = xy; m2[4] = xz; m2[5] = yz;
 }
-
-// Explicitly rounded products and fused multiply-adds.  The per-node forward
-// arithmetic (moments, closure, blend, samples) is written with them, in a
-// fixed order, wherever a product meets a sum: the compiler then has no
-// contraction left to choose, and every kernel that inlines it (interior,
-// face, TMA-staged, persistent, the step that writes a moment checkpoint, the
-// checkpoint decoder) computes the same bits.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 template <class L, class R>
 __device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<L, R>& M) {
@@ -611,6 +600,45 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   if (i != kNone) {
     const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
     forward_node<L, R, true, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, k, bj, bm);
+  }
+  if (A.sample) {
+    block_sum2<R>(bj, bm);
+    sample_commit(double(bj), double(bm), A.blk, blk0 + blockIdx.x);
+  }
+}
+
+// 2D face rows of one slice in face-table order: the y = 0 row, the
+// (x = 0, x = nx-1) pairs of rows 1 .. ny-2, the y = ny-1 row (nx, ny >= 2).
+__device__ __forceinline__ bool face2d_coords(const Geo& g, unsigned j, int& x, int& y) {
+  const unsigned nx = unsigned(g.nx), side = 2u * unsigned(g.ny - 2);
+  if (j < nx) { x = int(j); y = 0; return true; }
+  j -= nx;
+  if (j < side) { y = 1 + int(j >> 1); x = (j & 1u) ? g.nx - 1 : 0; return true; }
+  j -= side;
+  if (j < nx) { x = int(j); y = g.ny - 1; return true; }
+  return false;
+}
+
+// D2Q9 face nodes with positions and sources from the geometry: one dependent
+// load level (the populations), like the interior kernel, where the table
+// path needs two (table, then populations).  Rows, blocks and block sums are
+// those of fwd_face_kernel (rows_per_slice = face blocks per slice x kBlock).
+template <class L, class R, bool MOM = false>
+__global__ void __launch_bounds__(kBlock) fwd_face2d_kernel(FwdArgs<R> A, unsigned blk0, unsigned rows_per_slice) {
+  pdl_enter();
+  const Geo& g = A.geo;
+  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
+  const unsigned z = k / rows_per_slice;
+  R bj = 0, bm = 0;
+  int x, y;
+  if (z < unsigned(g.nz) && face2d_coords(g, k - z * rows_per_slice, x, y)) {
+    const unsigned i = unsigned(x) + unsigned(y) * g.sy + z * g.sz;
+    const uint8_t cls = A.cls[i];
+    const R u0 = R(A.uin[unsigned(y) + unsigned(g.ny) * z]);
+    const FwdStep<R> P{A.src, A.dst, A.sample, A.mom};
+    R f[L::Q];
+    gather_geo<L, R>(P.src, g, x, y, int(z), cls, cls == INLET ? u0 : R(0), A.ph.rho_out, f);
+    forward_core<L, R, MOM>(A, P, x, y, int(z), i, f, bj, bm);
   }
   if (A.sample) {
     block_sum2<R>(bj, bm);

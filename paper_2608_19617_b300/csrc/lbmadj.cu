@@ -413,6 +413,7 @@ struct ImplT final : Impl {
                           c->lay.nface};
   }
   bool has_interior() const { return c->lay.igx > 0 && c->lay.igy > 0 && c->lay.igz > 0; }
+  bool face2d() const { return L::D == 2 && c->cfg.nx >= 2 && c->cfg.ny >= 2; }
   // Step kernels: optionally with programmatic stream serialization, so that a
   // launch overlaps the tail of its predecessor (the kernel waits in
   // pdl_enter before touching data).
@@ -513,8 +514,21 @@ struct ImplT final : Impl {
           else launch(lbm::fwd_interior_kernel<L, R, false>, igrid(), st, A);
         },
         [&](cudaStream_t st) {
-          if (mom) launch(lbm::fwd_face_kernel<L, R, true>, dim3(c->lay.face_blocks), st, A, blk0);
-          else launch(lbm::fwd_face_kernel<L, R, false>, dim3(c->lay.face_blocks), st, A, blk0);
+          // D2Q9: face positions and sources from the geometry (one load level); D3Q19: the face table
+          const dim3 fg(c->lay.face_blocks);
+          if constexpr (L::D == 2) {
+            if (face2d()) {
+              const unsigned rows = unsigned(c->lay.fbs) * lbm::kBlock;
+              if (mom) launch(lbm::fwd_face2d_kernel<L, R, true>, fg, st, A, blk0, rows);
+              else launch(lbm::fwd_face2d_kernel<L, R, false>, fg, st, A, blk0, rows);
+              return;
+            }
+          }
+          if (mom) {
+            launch(lbm::fwd_face_kernel<L, R, true>, fg, st, A, blk0);
+          } else {
+            launch(lbm::fwd_face_kernel<L, R, false>, fg, st, A, blk0);
+          }
         });
   }
 

@@ -421,6 +421,32 @@ __device__ __forceinline__ void sample_commit(double bj, double bm, double* blk)
   sample_commit(bj, bm, blk, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
+// The per-step kernels fetch their block's running sums when a sampled step
+// starts: thread 0 issues a 32-byte asynchronous copy into shared memory, so
+// the read overlaps the block's population loads instead of trailing its last
+// reduction (the block keeps its slot on the SM until thread 0 is done).  The
+// sums and their arithmetic are those of sample_commit.
+__device__ __forceinline__ void sample_fetch(Sums* sh, const double* blk, unsigned bid) {
+  if (threadIdx.x == 0) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(sh));
+    const size_t src = __cvta_generic_to_global(blk + 4 * size_t(bid));
+    asm volatile(
+        "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+        "cp.async.cg.shared.global [%2], [%3], 16;\n\t"
+        "cp.async.commit_group;" ::"r"(d), "l"(src), "r"(d + 16u), "l"(src + 16) : "memory");
+  }
+}
+
+__device__ __forceinline__ void sample_commit_fetched(double bj, double bm, const Sums* sh, double* blk, unsigned bid) {
+  if (threadIdx.x == 0) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    Sums a = *sh;
+    neumaier(a.x, a.y, bj);
+    neumaier(a.z, a.w, bm);
+    reinterpret_cast<Sums*>(blk)[bid] = a;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Forward step.
 // ---------------------------------------------------------------------------
@@ -580,12 +606,15 @@ __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
   const Geo& g = A.geo;
   const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
   const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
+  __shared__ __align__(16) Sums sums;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (A.sample) sample_fetch(&sums, A.blk, bid);   // uniform across the grid
   R bj = 0, bm = 0;
   if (x < g.nx - 1)
     forward_node<L, R, false, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
-  if (A.sample) {   // uniform across the grid
+  if (A.sample) {
     block_sum2<R>(bj, bm);
-    sample_commit(double(bj), double(bm), A.blk);
+    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, bid);
   }
 }
 
@@ -595,6 +624,8 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   pdl_enter();
   const Geo& g = A.geo;
   const unsigned k = blockIdx.x * kBlock + threadIdx.x;
+  __shared__ __align__(16) Sums sums;
+  if (A.sample) sample_fetch(&sums, A.blk, blk0 + blockIdx.x);
   R bj = 0, bm = 0;
   const unsigned i = k < A.ft.n ? A.ft.idx[k] : kNone;   // rows padded per slice hold kNone
   if (i != kNone) {
@@ -603,7 +634,7 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   }
   if (A.sample) {
     block_sum2<R>(bj, bm);
-    sample_commit(double(bj), double(bm), A.blk, blk0 + blockIdx.x);
+    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, blk0 + blockIdx.x);
   }
 }
 
@@ -619,6 +650,20 @@ __device__ __forceinline__ bool face2d_coords(const Geo& g, unsigned j, int& x, 
   return false;
 }
 
+// One face node with its sources from the geometry: class and inlet velocity
+// from the node arrays, populations through gather_geo().
+template <class L, class R, bool MOM>
+__device__ __forceinline__ void face_geo_node(const FwdArgs<R>& A, int x, int y, int z, R& bj, R& bm) {
+  const Geo& g = A.geo;
+  const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
+  const uint8_t cls = A.cls[i];
+  const R u0 = cls == INLET ? R(A.uin[unsigned(y) + unsigned(g.ny) * unsigned(z)]) : R(0);
+  const FwdStep<R> P{A.src, A.dst, A.sample, A.mom};
+  R f[L::Q];
+  gather_geo<L, R>(P.src, g, x, y, z, cls, u0, A.ph.rho_out, f);
+  forward_core<L, R, MOM>(A, P, x, y, z, i, f, bj, bm);
+}
+
 // D2Q9 face nodes with positions and sources from the geometry: one dependent
 // load level (the populations), like the interior kernel, where the table
 // path needs two (table, then populations).  Rows, blocks and block sums are
@@ -629,20 +674,50 @@ __global__ void __launch_bounds__(kBlock) fwd_face2d_kernel(FwdArgs<R> A, unsign
   const Geo& g = A.geo;
   const unsigned k = blockIdx.x * kBlock + threadIdx.x;
   const unsigned z = k / rows_per_slice;
+  __shared__ __align__(16) Sums sums;
+  if (A.sample) sample_fetch(&sums, A.blk, blk0 + blockIdx.x);
   R bj = 0, bm = 0;
   int x, y;
-  if (z < unsigned(g.nz) && face2d_coords(g, k - z * rows_per_slice, x, y)) {
-    const unsigned i = unsigned(x) + unsigned(y) * g.sy + z * g.sz;
-    const uint8_t cls = A.cls[i];
-    const R u0 = R(A.uin[unsigned(y) + unsigned(g.ny) * z]);
-    const FwdStep<R> P{A.src, A.dst, A.sample, A.mom};
-    R f[L::Q];
-    gather_geo<L, R>(P.src, g, x, y, int(z), cls, cls == INLET ? u0 : R(0), A.ph.rho_out, f);
-    forward_core<L, R, MOM>(A, P, x, y, int(z), i, f, bj, bm);
-  }
+  if (z < unsigned(g.nz) && face2d_coords(g, k - z * rows_per_slice, x, y))
+    face_geo_node<L, R, MOM>(A, x, y, int(z), bj, bm);
   if (A.sample) {
     block_sum2<R>(bj, bm);
-    sample_commit(double(bj), double(bm), A.blk, blk0 + blockIdx.x);
+    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, blk0 + blockIdx.x);
+  }
+}
+
+// 3D face rows in face-table (ascending node) order: the z = 0 plane, the
+// rings of faces of slices 1 .. nz-2 (each in 2D face order), the z = nz-1
+// plane (nx, ny, nz >= 2).
+__device__ __forceinline__ bool face3d_coords(const Geo& g, unsigned k, int& x, int& y, int& z) {
+  const unsigned nx = unsigned(g.nx), plane = nx * unsigned(g.ny);
+  const unsigned ring = 2u * nx + 2u * unsigned(g.ny - 2), mid = ring * unsigned(g.nz - 2);
+  if (k < plane) { x = int(k % nx); y = int(k / nx); z = 0; return true; }
+  k -= plane;
+  if (k < mid) {
+    const unsigned s = k / ring;
+    z = 1 + int(s);
+    return face2d_coords(g, k - s * ring, x, y);
+  }
+  k -= mid;
+  if (k < plane) { x = int(k % nx); y = int(k / nx); z = g.nz - 1; return true; }
+  return false;
+}
+
+// D3Q19 face nodes from the geometry (the counterpart of fwd_face2d_kernel):
+// rows, blocks and block sums are those of fwd_face_kernel.
+template <class L, class R, bool MOM = false>
+__global__ void __launch_bounds__(kBlock) fwd_face3d_kernel(FwdArgs<R> A, unsigned blk0) {
+  pdl_enter();
+  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
+  __shared__ __align__(16) Sums sums;
+  if (A.sample) sample_fetch(&sums, A.blk, blk0 + blockIdx.x);
+  R bj = 0, bm = 0;
+  int x, y, z;
+  if (face3d_coords(A.geo, k, x, y, z)) face_geo_node<L, R, MOM>(A, x, y, z, bj, bm);
+  if (A.sample) {
+    block_sum2<R>(bj, bm);
+    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, blk0 + blockIdx.x);
   }
 }
 

@@ -414,6 +414,7 @@ struct ImplT final : Impl {
   }
   bool has_interior() const { return c->lay.igx > 0 && c->lay.igy > 0 && c->lay.igz > 0; }
   bool face2d() const { return L::D == 2 && c->cfg.nx >= 2 && c->cfg.ny >= 2; }
+  bool face3d() const { return L::D == 3 && c->cfg.nx >= 2 && c->cfg.ny >= 2 && c->cfg.nz >= 2; }
   // Step kernels: optionally with programmatic stream serialization, so that a
   // launch overlaps the tail of its predecessor (the kernel waits in
   // pdl_enter before touching data).
@@ -514,13 +515,20 @@ struct ImplT final : Impl {
           else launch(lbm::fwd_interior_kernel<L, R, false>, igrid(), st, A);
         },
         [&](cudaStream_t st) {
-          // D2Q9: face positions and sources from the geometry (one load level); D3Q19: the face table
+          // face positions and sources from the geometry (one load level); the face table on
+          // degenerate lattices
           const dim3 fg(c->lay.face_blocks);
           if constexpr (L::D == 2) {
             if (face2d()) {
               const unsigned rows = unsigned(c->lay.fbs) * lbm::kBlock;
               if (mom) launch(lbm::fwd_face2d_kernel<L, R, true>, fg, st, A, blk0, rows);
               else launch(lbm::fwd_face2d_kernel<L, R, false>, fg, st, A, blk0, rows);
+              return;
+            }
+          } else {
+            if (face3d()) {
+              if (mom) launch(lbm::fwd_face3d_kernel<L, R, true>, fg, st, A, blk0);
+              else launch(lbm::fwd_face3d_kernel<L, R, false>, fg, st, A, blk0);
               return;
             }
           }

@@ -157,6 +157,45 @@ def test_persistent_segments_at_full_size(name):
     assert r1[0] == pytest.approx(r0[0], rel=1e-5) and r1[1] == pytest.approx(r0[1], rel=1e-5)
 
 
+def _forward_states(case, prec, p0, windows):
+    out = []
+    for flow in (False, True):
+        sol = B.Solver(case, prec)
+        if flow:
+            sol.set_flow(True)
+        sol.set_state(p0)
+        for _ in range(windows):
+            sol.step_window()
+        out.append(sol.get_state())
+        sol.close()
+    return out
+
+
+@pytest.mark.parametrize("name", ["d2-zouhe-fp32", "d2-zerograd-every3-fp64", "d3-pressure-fp32",
+                                  "d3-diss-periodicz-fp64"])
+def test_geometric_face_nodes_match_the_face_table_bitwise(name):
+    """The per-step face kernels take a face node's position, class and
+    sources from the geometry; the persistent kernels read them from the
+    host-built face table.  The node arithmetic is explicitly rounded, so the
+    forward states agree bit for bit (a wrong source, mask or inlet velocity
+    would not)."""
+    make, prec = CASES[name]
+    case = make()
+    if prec == B.LBM_FP32:
+        case = f32_inputs(case)
+    s0, s1 = _forward_states(case, prec, _start(case), 2)
+    assert np.array_equal(s0, s1)
+
+
+def test_geometric_face_nodes_match_the_face_table_on_the_ubend():
+    """Full-size U-bend (velocity inlet and zero-gradient outlet on the x = 0
+    face, walls elsewhere): geometric and table face nodes, bit for bit."""
+    case = I.WORKLOADS["ubend256x128x64"]()
+    case = case.replace(window_len=20, ckpt_every=10)
+    s0, s1 = _forward_states(case, B.LBM_FP32, _advanced(case, 60), 1)
+    assert np.array_equal(s0, s1)
+
+
 def test_persistent_segments_are_rejected_for_batches():
     case = I.stack_cases([I.small_channel(64, 10, window_len=4, ckpt_every=2) for _ in range(2)])
     sol = B.Solver(case, B.LBM_FP32)

@@ -208,10 +208,16 @@ def whole_job_mlups(lus_per_step_per_rank, steps, world, ms_max):
     return world * steps * lus_per_step_per_rank / (ms_max / 1e3) / 1e6
 
 
+def fwd_face_kernel(case):
+    """The forward face kernel the library launches for this lattice (face
+    positions from the geometry; the workloads have every extent >= 2)."""
+    return "fwd_face2d_kernel" if case.lattice == 9 else "fwd_face3d_kernel"
+
+
 def unit_traffic(unit, case, K):
     """ncu DRAM bytes of one unit of work, from profiles/traffic.json (None if
     any kernel involved has no capture for the current source)."""
-    fwd = [measured_traffic(k, case.name) for k in ("fwd_interior_kernel", "fwd_face_kernel")]
+    fwd = [measured_traffic(k, case.name) for k in ("fwd_interior_kernel", fwd_face_kernel(case))]
     adj = [measured_traffic(k, case.name) for k in ("adj_interior_kernel", "adj_face_kernel")]
     if unit == "forward step":
         return None if None in fwd else sum(fwd)
@@ -406,14 +412,14 @@ def run_ours(args, case, rank, world, local):
             bpl = bytes_per_lu(case, ph, rs=rs) * n
             phase_rows[ph] = {"steps": t["launches"], "ms": t["ms"], "avg_step_us": 1e3 * avg_ms,
                               "bytes_per_step": bpl, "gbs": bpl / (avg_ms / 1e3) / 1e9}
-    # Units of the roofline (SURVEY 8d): a forward step, and an adjoint-sweep
+    # Units of the roofline: a forward step, and an adjoint-sweep
     # step = one adjoint step plus its share (K-1)/K of a recompute step.  The
     # sweep is timed whole (events around lbm_adjoint_window), since recompute
     # and adjoint steps may run concurrently.
     sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / len(sweep_ev)
     sweep_b = (bytes_per_lu(case, "adjoint", rs=rs) + bytes_per_lu(case, "recompute", rs=rs) * (K - 1) / K) * n
     fk = ("fwd_flow_kernel" if args.flow else
-          "fwd_tma_kernel+fwd_face_kernel" if args.tma else "fwd_interior_kernel+fwd_face_kernel")
+          ("fwd_tma_kernel+" if args.tma else "fwd_interior_kernel+") + fwd_face_kernel(case))
     ak = "adj_flow_kernel" if args.flow else "adj_interior_kernel+adj_face_kernel"
     units = {
         "forward step": {"bytes": bytes_per_lu(case, "forward", rs=rs) * n,

@@ -37,6 +37,11 @@ design notes):
   phi = 1 - gamma;
 * a window of |W| steps samples f^n at the steps n0, n0+dW, ...; the objective
   source enters the adjoint at those steps with weight dW/|W| (Eq. 42);
+* full-time adjoint (Sec. 4.2.3, the comparison with full-time adjoint
+  optimization): the run from the initial time is one window of T steps whose
+  samples start at step T - |W| (case.sample_from), so the objective is the
+  mean over the final |W| steps while the adjoint is traced back to step 0;
+  the weight is then dW/(T - sample_from);
 * D3Q19 (beyond the paper): same collision with p,q in {x,y,z}; velocity
   inlet by the linear moving-wall bounce-back f_a = f_abar + 2 w_a rho0 c_a.u/cs^2
   with rho0 = 1; zero-gradient outlet copies the neighbour along the inward normal.
@@ -191,7 +196,7 @@ class Problem:
     ``case`` is any object with the attributes of ``inputs.Case`` (lattice, nx,
     ny, nz, tau, cs_smag, node_class, gamma, inlet_u, obj_weights, obj_kind,
     obj_uref, q_interp, g_max, rho_out, periodic, monitor_kind, monitor_u,
-    monitor_l, window_len, sample_every, conv_tol).
+    monitor_l, window_len, sample_every, sample_from, conv_tol).
     """
 
     def __init__(self, case):
@@ -382,21 +387,32 @@ class Problem:
         objective and the monitor, and (if store) the carried fields
         p^{n0-1} ... p^{n0+|W|-1} of the window.
         """
-        W, dW = int(self.case.window_len), int(self.case.sample_every)
+        W = int(self.case.window_len)
         g = self.g(gamma)
         p = p_start
         traj = [p] if store else None
         js, ms = [], []
         for k in range(W):
             f, h, p, aux = self.step(p, g)
-            if k % dW == 0:
+            if self.sampled(k):
                 j, m = self.sample(f, h, aux, g)
                 js.append(j)
                 ms.append(m)
             if store:
                 traj.append(p)
-        weight = dW / W
+        weight = self.sample_weight()
         return p, weight * sum(js), weight * sum(ms), traj
+
+    def sampled(self, k):
+        """Is step k of the window a sampling instant?  Every dW-th step from
+        the first sampled step s0 on (s0 = 0 for the plain window of Eq. 42,
+        s0 = T - |W| for the full-time run of Sec. 4.2.3)."""
+        s0, dW = int(self.case.sample_from), int(self.case.sample_every)
+        return k >= s0 and (k - s0) % dW == 0
+
+    def sample_weight(self):
+        """dW over the sampled span (Eq. 42): 1 / number of samples."""
+        return int(self.case.sample_every) / (int(self.case.window_len) - int(self.case.sample_from))
 
     def run_until_converged(self, p_start=None, gamma=None, max_windows=None):
         """Consecutive windows until Eq. 26 holds (Alg. 1); returns the record."""
@@ -485,8 +501,8 @@ class Problem:
         with the paper's lambda = -a), dJ/dgamma = -dJ/dphi, and a = dJ/dp^{n0-1}.
         """
         lat, case = self.lat, self.case
-        W, dW = int(case.window_len), int(case.sample_every)
-        weight = dW / W
+        W = int(case.window_len)
+        weight = self.sample_weight()
         g = self.g(gamma)
         phi = self.phi(gamma)
         dg = dg_dphi(phi, case.q_interp, case.g_max)
@@ -499,7 +515,7 @@ class Problem:
             grad_phi += dg * (a * (h[lat.opp] - h)).sum(axis=0)
             jac, jaux = self.local_jacobian(f, h, aux, g)
             b = np.einsum("ban,bn->an", jac, a)                  # Eq. 35
-            if k % dW == 0:
+            if self.sampled(k):
                 src, dphi = self.objective_source(f, h, aux, g, phi, jaux)
                 b = b + weight * src
                 grad_phi += weight * dphi

@@ -60,6 +60,7 @@ class Case:
     monitor_l: float = 1.0          # reference length of the drag coefficient
     window_len: int = 200
     sample_every: int = 1
+    sample_from: int = 0            # first sampled step of a window (full-time runs: T - |W|)
     conv_tol: float = 1e-3
     ckpt_every: int = 200
     ckpt_format: int = CKPT_NATIVE

@@ -67,6 +67,14 @@ def parse():
                     help="persistent launches: one cooperative kernel per checkpoint segment")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: no CPU baseline, no FP64 check, no e2e pass")
+    ap.add_argument("--full-time", action="store_true",
+                    help="Sec. 4.2.3 comparison instead of the throughput line: one design gradient by the "
+                         "consecutive-window framework against the full-time adjoint (default workload "
+                         "cylinder200x100)")
+    ap.add_argument("--full-time-k", type=int, default=1,
+                    help="checkpoint interval of the full-time run (1: the complete history)")
+    ap.add_argument("--full-time-cap-gb", type=float, default=96.0,
+                    help="largest device workspace the full-time run may take")
     a = ap.parse_args()
     if a.quick:
         a.no_cpu_baseline = a.no_fp64_check = True
@@ -533,10 +541,103 @@ def run_ours(args, case, rank, world, local):
     return 0
 
 
+def run_full_time(args, case):
+    """The comparison of Sec. 4.2.3 (its table of time per iteration and
+    storage), for one design gradient from the initial field:
+
+    * window framework: windows of |W| steps until the consecutive-window test
+      of Eq. 26 holds (at most case.max_windows), then the adjoint of the last
+      window only (checkpoints of that window, K = case.ckpt_every);
+    * full-time adjoint: the same n |W| steps as one window whose samples are
+      the last |W| steps (lbm_set_sample_start), every state kept
+      (K = --full-time-k, 1 = the complete history), the adjoint traced back to
+      the initial time.
+
+    Both start from the same field, so the objectives agree bit for bit; the
+    gradients differ by the sensitivity carried through the transient.  Times
+    are host wall clock around the synchronised calls (the window arm after one
+    warm-up iteration that captures its graphs; the full-time arm launches
+    directly, since its window would make a graph of some 10^5 nodes).
+    Storage is the device workspace each context takes."""
+    import numpy as np
+    import torch
+    from paper_2608_19617_b300 import binding as B
+    B.lib()
+    prec = B.LBM_FP64 if args.precision == "fp64" else B.LBM_FP32
+    W = case.window_len
+    win = B.Solver(case, prec, pipeline=args.pipeline)
+    win.set_graphs(bool(args.graphs))
+    p_init = win.get_state()
+
+    def window_iteration():
+        win.set_state(p_init)
+        n, conv, ratio, J = 0, False, float("inf"), None
+        while n < case.max_windows:
+            J, _ = win.step_window()
+            n += 1
+            conv, ratio = win.window_converged()
+            if conv:
+                break
+        win.adjoint_window()
+        return n, conv, ratio, J, win.design_gradient()
+
+    window_iteration()                       # warm-up: graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n, conv, ratio, J_win, g_win = window_iteration()
+    torch.cuda.synchronize()
+    t_win = time.perf_counter() - t0
+    ws_win = int(win.workspace.numel())
+    win.close()
+
+    T = n * W
+    K = args.full_time_k
+    if T % K:
+        raise SystemExit(f"--full-time-k {K} must divide the run length {T}")
+    ft = case.replace(window_len=T, ckpt_every=K, sample_from=T - W)
+    ws_full = B.workspace_size(B.config_from_case(ft, prec, pipeline=args.pipeline))
+    out = {"metric": "time per design gradient and storage: consecutive-window framework vs full-time adjoint "
+                     "(Sec. 4.2.3)",
+           "impl": "ours", "dtype": "f64" if prec == B.LBM_FP64 else "f32", "data": "synthetic",
+           "config": {"workload": case.name, "window_len": W, "sample_every": case.sample_every,
+                      "ckpt_every_window": case.ckpt_every, "ckpt_every_full_time": K,
+                      "pipeline": bool(args.pipeline), "graphs_window": bool(args.graphs)},
+           "window": {"windows": n, "converged": bool(conv), "ratio": ratio, "steps_forward": T,
+                      "steps_adjoint": W, "seconds": t_win, "workspace_bytes": ws_win, "J": J_win},
+           "paper": {"minutes_per_iteration": {"full_time": 1.63, "window": 0.663},
+                     "storage": {"full_time": "558 GB", "window": "217 MB"}}}
+    if ws_full > args.full_time_cap_gb * 1e9:
+        out["full_time"] = {"skipped": f"workspace {ws_full / 1e9:.1f} GB above --full-time-cap-gb"}
+        print(json.dumps(out))
+        return 0
+    full = B.Solver(ft, prec, pipeline=args.pipeline)
+    full.set_graphs(False)
+    full.set_state(p_init)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J_full, _ = full.step_window()
+    full.adjoint_window()
+    g_full = full.design_gradient()
+    torch.cuda.synchronize()
+    t_full = time.perf_counter() - t0
+    full.close()
+    m = np.abs(g_win) + np.abs(g_full) > 0
+    cos = float(g_win[m] @ g_full[m] / (np.linalg.norm(g_win[m]) * np.linalg.norm(g_full[m])))
+    out["full_time"] = {"steps_forward": T, "steps_adjoint": T, "seconds": t_full, "workspace_bytes": ws_full,
+                        "J": J_full}
+    out.update({"time_ratio": t_full / t_win, "storage_ratio": ws_full / ws_win,
+                "J_bitwise_equal": J_full == J_win, "grad_cosine": cos,
+                "grad_rel_diff": float(np.linalg.norm(g_full - g_win) / np.linalg.norm(g_full))})
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     from paper_2608_19617_b300 import inputs as I
+    if args.full_time and args.workload == WORKLOAD:
+        args.workload = "cylinder200x100"
     case = I.WORKLOADS[args.workload]()
     if args.window_len or args.ckpt_every:
         wl = args.window_len or case.window_len
@@ -546,6 +647,8 @@ def main():
     if args.impl == "reference":
         rc = run_reference(args, case, rank, world)
         return rc
+    if args.full_time:
+        return run_full_time(args, case) if rank == 0 else 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

@@ -287,6 +287,23 @@ lbm_status lbm_set_flow(lbm_ctx* ctx, int32_t enable);
  * LBM_ERR_CUDA. */
 lbm_status lbm_set_tma(lbm_ctx* ctx, int32_t enable);
 
+/* First sampled step of each following window: the objective and monitor
+ * means (Eq. 42) and the adjoint's objective sources use the steps first,
+ * first + sample_every, ... < window_len, weighted by
+ * sample_every / (window_len - first).  0 (the default) is the window of the
+ * consecutive-window scheme (Sec. 3.1).  A window of T steps run from the
+ * initial field with first = T - |W| is the full-time adjoint of Sec. 4.2.3
+ * (the comparison with full-time adjoint optimization): the objective is the
+ * mean over the final |W| steps, the whole history is checkpointed, and
+ * lbm_adjoint_window traces the adjoint back to the initial time.  Its J
+ * equals, bit for bit, that of a |W|-step window after the same T - |W|
+ * unsampled steps.  Invalidates the recorded window and gradient; the
+ * consecutive-window test keeps comparing successive windows as sampled.
+ * Errors: LBM_ERR_ARG unless 0 <= first < window_len and
+ * (window_len - first) is a multiple of sample_every.  The no-allocation
+ * entry point always samples from step 0. */
+lbm_status lbm_set_sample_start(lbm_ctx* ctx, int32_t first);
+
 /* Test hook of the persistent kernels' bounded waits: the longest wait without
  * progress (seconds, default 4) and one band that computes but never
  * publishes its progress (-1, the default: none), so that its neighbours'

@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
         "lbm_set_pdl": (st, [c_void_p, c_int32]),
         "lbm_set_flow": (st, [c_void_p, c_int32]),
         "lbm_set_tma": (st, [c_void_p, c_int32]),
+        "lbm_set_sample_start": (st, [c_void_p, c_int32]),
         "lbm_get_schedule": (st, [c_void_p, POINTER(LbmSchedule)]),
         "lbm_set_flow_test_hook": (st, [c_void_p, c_double, c_int32]),
         "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -186,6 +187,8 @@ class Solver:
                                self.workspace.data_ptr(), size, c_void_p(self.stream.cuda_stream),
                                byref(ctx)), "lbm_create")
         self.ctx = ctx
+        if int(getattr(case, "sample_from", 0)):
+            self.set_sample_start(case.sample_from)
 
     # -- C calls --------------------------------------------------------------
     def step_window(self):
@@ -292,6 +295,11 @@ class Solver:
     def set_tma(self, enable: bool):
         """TMA-staged interior forward steps (lbm_set_tma)."""
         check(lib().lbm_set_tma(self.ctx, int(bool(enable))), "lbm_set_tma")
+
+    def set_sample_start(self, first: int):
+        """First sampled step of each following window (lbm_set_sample_start);
+        a full-time run of T steps samples from T - |W|."""
+        check(lib().lbm_set_sample_start(self.ctx, int(first)), "lbm_set_sample_start")
 
     def set_flow_test_hook(self, wait_seconds: float = 4.0, silent_band: int = -1):
         """Bounded-wait test hook of the persistent kernels (lbm_set_flow_test_hook)."""

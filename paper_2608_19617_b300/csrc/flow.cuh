@@ -109,6 +109,13 @@ __device__ __forceinline__ void flow_publish(const Flow& fl, unsigned b, int val
   if (threadIdx.x == 0 && int(b) != fl.silent) st_release_gpu(fl.done + b, value);
 }
 
+// Sampling instants of a window (Eq. 42): every dW-th step from the first
+// sampled step s0 on; s0 = 0 for a window of the consecutive-window scheme,
+// s0 = T - |W| for a full-time run of T steps (Sec. 4.2.3).  dW = 0: never.
+__host__ __device__ __forceinline__ bool sampled_step(int step, int s0, int dW) {
+  return dW > 0 && step >= s0 && (step - s0) % dW == 0;
+}
+
 // Step the coordinates of a node forward by kFlowBlock indices.
 __device__ __forceinline__ void flow_advance(const Geo& g, int& x, int& y, int& z) {
   x += kFlowBlock;
@@ -153,7 +160,7 @@ __device__ __noinline__ void adj_face_node(const AdjArgs<R>& A, const AdjStep<R>
 // sample_every == 0: nothing is sampled).
 template <class L, class R>
 __global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 1)
-    fwd_flow_kernel(FwdArgs<R> A, Chain<R> ch, Flow fl, int nsteps, int step0, int sample_every) {
+    fwd_flow_kernel(FwdArgs<R> A, Chain<R> ch, Flow fl, int nsteps, int step0, int sample_every, int sample_from) {
   const Geo& g = A.geo;
   const unsigned b = blockIdx.x;
   const unsigned i0 = fl.band[b], i1 = fl.band[b + 1], f0 = fl.fband[b], f1 = fl.fband[b + 1];
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 
   for (int k = 0; k < nsteps; ++k) {
     if (k > 0 && !flow_wait(fl, b, k)) break;
     // A.mom: moment checkpoint of the launch's last output
-    const FwdStep<R> P{ch.src(k), ch.dst(k), sample_every > 0 && (step0 + k) % sample_every == 0,
+    const FwdStep<R> P{ch.src(k), ch.dst(k), sampled_step(step0 + k, sample_from, sample_every),
                        k == nsteps - 1 ? A.mom : nullptr};
     R bj = 0, bm = 0;
     int x = x0, y = y0, z = z0;
@@ -202,7 +209,7 @@ struct AdjChain {
 
 template <class L, class R>
 __global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 1)
-    adj_flow_kernel(AdjArgs<R> A, AdjChain<R> ch, Flow fl, int nsteps, int step0, int sample_every) {
+    adj_flow_kernel(AdjArgs<R> A, AdjChain<R> ch, Flow fl, int nsteps, int step0, int sample_every, int sample_from) {
   const Geo& g = A.geo;
   const unsigned b = blockIdx.x;
   const unsigned i0 = fl.band[b], i1 = fl.band[b + 1], f0 = fl.fband[b], f1 = fl.fband[b + 1];
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(kFlowBlock, sizeof(R) == 4 ? kFlowMinBlocks : 
     const AdjStep<R> P{k == 0 ? ch.bnext0 : ((k & 1) ? ch.o0 : ch.o1),
                        j == 0 ? ch.p0 : ch.p1 + (long long)(j - 1) * ch.stride,
                        (k & 1) ? ch.o1 : ch.o0,
-                       (step0 + j) % sample_every == 0,
+                       sampled_step(step0 + j, sample_from, sample_every),
                        k == 0 && ch.bnext0 == nullptr};
     int x = x0, y = y0, z = z0;
 #pragma unroll 1

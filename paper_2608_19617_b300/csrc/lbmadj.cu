@@ -293,6 +293,7 @@ struct lbm_ctx {
   int converged = 0, nwin_for_ratio = 0;
   int bout_last = 0;          // adjoint buffer holding b^{n0}
   double jconst = 0;
+  int sample_from = 0;        // first sampled step of a window (lbm_set_sample_start)
   bool timing = false;
   int64_t timing_failures = 0;
   bool filtered = false;      // design set through lbm_set_design_filtered
@@ -459,7 +460,7 @@ struct ImplT final : Impl {
     o.mon = k.monitor_kind;
     for (int i = 0; i < 3; ++i) o.uref[i] = R(k.objective_uref[i]);
     for (int i = 0; i < 6; ++i) o.box[i] = k.obj_box[i];
-    o.ws = R(double(k.sample_every) / double(k.window_len));
+    o.ws = R(double(k.sample_every) / double(k.window_len - c->sample_from));   // 1 / samples
     return o;
   }
 
@@ -672,7 +673,7 @@ struct ImplT final : Impl {
   void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every, void* mom) override {
     const lbm::FwdArgs<R> A = fwd_args(nullptr, nullptr, 0, mom);
     const lbm::Chain<R> ch{static_cast<R*>(a), static_cast<R*>(b), (long long)(stride_bytes / sizeof(R))};
-    launch_flow(lbm::fwd_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, sample_every);
+    launch_flow(lbm::fwd_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, sample_every, c->sample_from);
   }
   void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
                int nsteps, int step0) override {
@@ -680,7 +681,7 @@ struct ImplT final : Impl {
     const lbm::AdjChain<R> ch{static_cast<const R*>(p0), static_cast<const R*>(p1),
                               (long long)(stride_bytes / sizeof(R)), static_cast<const R*>(bnext0),
                               static_cast<R*>(o0), static_cast<R*>(o1)};
-    launch_flow(lbm::adj_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, c->cfg.sample_every);
+    launch_flow(lbm::adj_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, c->cfg.sample_every, c->sample_from);
   }
   void pull(const void* b, void* out) override {
     lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(
@@ -845,7 +846,7 @@ lbm_status enqueue_window(lbm_ctx* c) {
     } else {
       for (int j = 0; j < K; ++j) {
         const int step = s * K + j;
-        c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), step % k.sample_every == 0,
+        c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), lbm::sampled_step(step, c->sample_from, k.sample_every),
                      j == K - 1 ? mom : nullptr);
         c->cur ^= 1;
       }
@@ -854,17 +855,18 @@ lbm_status enqueue_window(lbm_ctx* c) {
   }
   const double mon_scale =
       k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
+  const double nsamples = double((k.window_len - c->sample_from) / k.sample_every);
   if (k.lattice == LBM_D2Q9) {
     // persistent bands (single lattice only) sum as one flat run of block sums
     lbm::slice_end_kernel<<<k.nz, lbm::kEndThreads, 0, c->ls>>>(
         c->at<double>(c->lay.partials), c->lay.igx, c->lay.igy, c->lay.fbs, c->lay.igx * c->lay.igy * c->lay.igz,
-        double(k.window_len / k.sample_every), c->at<double>(c->lay.slice_c), mon_scale, k.monitor_kind,
+        nsamples, c->at<double>(c->lay.slice_c), mon_scale, k.monitor_kind,
         c->at<double>(c->lay.slice_j), c->use_flow ? c->lay.nblocks_sum : 0);
     c->kernels += 1;
   }
   lbm::window_end_kernel<<<1, lbm::kEndThreads, 0, c->ls>>>(
       c->at<double>(c->lay.partials), c->lay.nblocks_sum, c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol,
-      c->at<int>(c->lay.flags), double(k.window_len / k.sample_every), c->jconst, mon_scale, k.monitor_kind);
+      c->at<int>(c->lay.flags), nsamples, c->jconst, mon_scale, k.monitor_kind);
   c->kernels += 1;
   c->kernels_window = c->kernels - k0;
   return LBM_OK;
@@ -939,7 +941,7 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
     } else {
       for (int j = K - 1; j >= 0; --j) {
         const int step = s * K + j;
-        c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), step % k.sample_every == 0);
+        c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), lbm::sampled_step(step, c->sample_from, k.sample_every));
         bnext = c->adjbuf(bo);
         bo ^= 1;
       }
@@ -1640,6 +1642,22 @@ lbm_status lbm_set_tma(lbm_ctx* c, int32_t enable) {
     for (auto& g : c->gadj) c->drop_graph(g);
   }
   c->use_tma = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_sample_start(lbm_ctx* c, int32_t first) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  const lbm_config& k = c->cfg;
+  if (first < 0 || first >= k.window_len || (k.window_len - first) % k.sample_every)
+    return fail(LBM_ERR_ARG, "the first sampled step must lie in [0, window_len) with window_len - first a multiple of sample_every");
+  if (first != c->sample_from) {
+    // captured graphs hold the old sampling flags and weight: capture again on next use
+    for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);
+    for (auto& g : c->gadj) c->drop_graph(g);
+  }
+  c->sample_from = first;
+  c->window_valid = false;
+  c->grad_valid = false;
   return LBM_OK;
 }
 

@@ -279,6 +279,31 @@ def config_channel(seed=1001) -> Case:
                 ckpt_every=200, max_windows=10, design_box=(1, nx - 1, 1, ny - 1, 0, 1))
 
 
+def config_cylinder(re=51.2) -> Case:
+    """D2Q9 200x100 flow around a circular cylinder (the cylinder case of Sec. 4):
+    radius 8 at the domain centre with phi = 0.5 inside (gamma = 0.5), Re = 51.2
+    on the diameter by default (vortex shedding), uniform inlet u = 0.04 (the
+    paper gives no inlet speed), Zou-He pressure outlet, walls y = 0 and 99;
+    objective = the drag force over the design domain, the 32x32 square around
+    the cylinder; windows of 5000 steps sampled every 50 (Delta W), checkpoints
+    every 100, tolerance 1e-3 on the drag monitor."""
+    nx, ny = 200, 100
+    cls = channel_classes(nx, ny, outlet=OUTLET_P)
+    gamma = np.where(disk_mask(nx, ny, 100, 50, 16), 0.5, 0.0)[None]
+    gamma[cls == WALL] = 1.0
+    uin = np.full((1, ny), 0.04)
+    uin[0, 0] = uin[0, ny - 1] = 0.0
+    box = (84, 116, 34, 66)
+    w = np.zeros((1, ny, nx))
+    w[0, box[2]:box[3], box[0]:box[1]] = 1.0
+    return Case(name="cylinder200x100", lattice=9, nx=nx, ny=ny, nz=1,
+                tau=tau_from_re(0.04, 16, re), cs_smag=0.1, node_class=cls, gamma=gamma,
+                inlet_u=uin, obj_weights=w, obj_kind=OBJ_DRAG, monitor_kind=MON_DRAG,
+                monitor_u=0.04, monitor_l=16.0, window_len=5000, sample_every=50,
+                conv_tol=1e-3, ckpt_every=100, max_windows=12,
+                design_box=(box[0], box[1], box[2], box[3], 0, 1))
+
+
 def config_wake(seed=1002) -> Case:
     """D2Q9 1024x256 cylinder wake: disk D=32 at (256,128), Re=200, uniform inlet
     u=0.04, Zou-He pressure outlet; design = min-max smooth noise (sigma 6) in
@@ -397,6 +422,7 @@ def config_ubend(seed=1004, big=False) -> Case:
 
 WORKLOADS = {
     "channel128x64": config_channel,
+    "cylinder200x100": config_cylinder,
     "wake1024x256": config_wake,
     "step2048x512": config_step,
     "ubend256x128x64": lambda: config_ubend(big=False),

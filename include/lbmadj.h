@@ -213,6 +213,21 @@ lbm_status lbm_set_design_filtered(lbm_ctx* ctx, const float* x_raw, const lbm_f
  * window or when the design was not set through the filter. */
 lbm_status lbm_design_gradient_filtered(lbm_ctx* ctx, double* grad, size_t n);
 
+/* Chain rule of the density filter and Heaviside projection (Sec. 3.3) for
+ * any sensitivity: dx = (d gamma / d x)^T dgamma, both host or device, double
+ * [N] (dgamma is read inside and outside design_box; outside, gamma = x).
+ * This is what lbm_design_gradient_filtered applies to dJ/dgamma; the
+ * optimization loop applies it to the volume constraint's gradient.
+ * Errors: LBM_ERR_STATE unless the design was set by lbm_set_design_filtered,
+ * LBM_ERR_ARG for n != N. */
+lbm_status lbm_filter_chain_rule(lbm_ctx* ctx, const double* dgamma, double* dx, size_t n);
+
+/* Volume fraction of Sec. 3.3, V = (1/n_D) sum over the design box of
+ * (1 - phi_i), i.e. the mean of the current gamma over design_box; its
+ * gradient with respect to gamma is 1/n_D inside the box.  FP64 sum in a
+ * fixed order.  Errors: LBM_ERR_ARG for an empty design box. */
+lbm_status lbm_design_volume(lbm_ctx* ctx, double* volume);
+
 /* The current (physical) design field gamma (host or device, float [N]). */
 lbm_status lbm_get_design(lbm_ctx* ctx, float* gamma, size_t n);
 
@@ -357,6 +372,47 @@ lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);
 lbm_status lbm_step_window_noalloc(const lbm_config* cfg, const uint8_t* node_class, const float* design_gamma,
                                    const float* objective_weights, const float* inlet_u, float* pop,
                                    float* pop_tmp, void* stream, double* J_window, double* monitor_window);
+
+/* ---- Design update: the Method of Moving Asymptotes ---------------------
+ * The optimization loop of the paper (Sec. 3.3, topology optimization
+ * procedure; Alg. 2) updates the design variables with MMA (Svanberg 1987)
+ * under the volume constraint.  An lbm_mma holds one run's state for n
+ * variables x in [xmin, xmax] and m constraints f_i(x) <= 0 (1 <= m <=
+ * LBM_MMA_MAX_M).  Each lbm_mma_update takes the objective and constraint
+ * values at x and their gradients, builds the moving asymptotes (x -/+ 0.5
+ * span at the first two iterations, then contracted by 0.7 where x_j
+ * oscillates and widened by 1.2 where it moves monotonically, kept within
+ * [0.01, 10] span of x_j), the move limits (10% of the way to each
+ * asymptote) and the convex separable approximations
+ * r_i + sum_j p_ij/(U_j - z_j) + q_ij/(z_j - L_j), and solves the resulting
+ * subproblem (with artificial variables of cost 1000 that keep it feasible)
+ * by the dual method in FP64.  The per-variable work runs on the device. */
+#define LBM_MMA_MAX_M 8
+typedef struct lbm_mma lbm_mma;
+
+/* Bytes of device workspace lbm_mma_create needs for n variables and m
+ * constraints.  Errors: LBM_ERR_ARG for n = 0 or m outside [1, LBM_MMA_MAX_M]. */
+lbm_status lbm_mma_workspace_size(size_t n, int32_t m, size_t* bytes);
+
+/* Start an MMA run.
+ *   xmin, xmax   host or device, double [n], finite, xmin < xmax (copied)
+ *   workspace    device, >= lbm_mma_workspace_size bytes, 256-byte aligned, owned
+ *                by the caller and kept alive until lbm_mma_destroy
+ *   stream       cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Errors: LBM_ERR_ARG, LBM_ERR_WORKSPACE, LBM_ERR_CUDA. */
+lbm_status lbm_mma_create(size_t n, int32_t m, const double* xmin, const double* xmax, void* workspace,
+                          size_t workspace_bytes, void* stream, lbm_mma** out);
+
+/* One MMA iteration.
+ *   x        device, double [n], in/out: the current point, replaced by the next
+ *   fval     host, double [m+1]: f_0(x) (the objective), then f_1(x) .. f_m(x)
+ *   dfdx     device, double [m+1][n]: the gradients, objective first
+ *   lam_out  host, double [m] or NULL: the subproblem's multipliers
+ * Synchronises the stream.  Errors: LBM_ERR_ARG (null pointers, non-finite
+ * fval), LBM_ERR_CUDA. */
+lbm_status lbm_mma_update(lbm_mma* mma, double* x, const double* fval, const double* dfdx, double* lam_out);
+
+lbm_status lbm_mma_destroy(lbm_mma* mma);
 
 const char* lbm_status_string(lbm_status s);
 const char* lbm_last_error(void);

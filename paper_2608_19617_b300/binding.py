@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "liblbmadj.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_WORKSPACE, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_NONFINITE, LBM_NOT_CONVERGED = range(7)
 LBM_FP32, LBM_FP64 = 0, 1
+LBM_MMA_MAX_M = 8
 NUM_PHASES = 4
 PHASES = ("forward", "recompute", "adjoint", "checkpoint")
 
@@ -96,6 +97,13 @@ def lib() -> ctypes.CDLL:
         "lbm_set_flow": (st, [c_void_p, c_int32]),
         "lbm_set_tma": (st, [c_void_p, c_int32]),
         "lbm_set_sample_start": (st, [c_void_p, c_int32]),
+        "lbm_filter_chain_rule": (st, [c_void_p, c_void_p, c_void_p, c_size_t]),
+        "lbm_design_volume": (st, [c_void_p, POINTER(c_double)]),
+        "lbm_mma_workspace_size": (st, [c_size_t, c_int32, POINTER(c_size_t)]),
+        "lbm_mma_create": (st, [c_size_t, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p,
+                                POINTER(c_void_p)]),
+        "lbm_mma_update": (st, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "lbm_mma_destroy": (st, [c_void_p]),
         "lbm_get_schedule": (st, [c_void_p, POINTER(LbmSchedule)]),
         "lbm_set_flow_test_hook": (st, [c_void_p, c_double, c_int32]),
         "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -296,6 +304,19 @@ class Solver:
         """TMA-staged interior forward steps (lbm_set_tma)."""
         check(lib().lbm_set_tma(self.ctx, int(bool(enable))), "lbm_set_tma")
 
+    def filter_chain_rule(self, dgamma, out=None):
+        """(d gamma / d x)^T dgamma through the filter and projection (lbm_filter_chain_rule)."""
+        dg = np.ascontiguousarray(dgamma, dtype=np.float64).reshape(-1)
+        out = np.empty(self.n) if out is None else out
+        check(lib().lbm_filter_chain_rule(self.ctx, _ptr(dg), _ptr(out), self.n), "lbm_filter_chain_rule")
+        return out
+
+    def design_volume(self) -> float:
+        """Mean gamma over the design box, V of Sec. 3.3 (lbm_design_volume)."""
+        v = c_double()
+        check(lib().lbm_design_volume(self.ctx, byref(v)), "lbm_design_volume")
+        return v.value
+
     def set_sample_start(self, first: int):
         """First sampled step of each following window (lbm_set_sample_start);
         a full-time run of T steps samples from T - |W|."""
@@ -333,6 +354,52 @@ class Solver:
         if getattr(self, "ctx", None):
             lib().lbm_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mma:
+    """One MMA run (lbm_mma_*): n design variables on the device, m
+    constraints f_i <= 0.  update() takes the point as a float64 CUDA tensor
+    (changed in place), the values [m+1] and the gradients [m+1][n]."""
+
+    def __init__(self, xmin, xmax, m: int, device="cuda", stream=None):
+        import torch
+
+        xmin = np.ascontiguousarray(xmin, dtype=np.float64).reshape(-1)
+        xmax = np.ascontiguousarray(xmax, dtype=np.float64).reshape(-1)
+        self.n, self.m = xmin.size, int(m)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        size = c_size_t()
+        check(lib().lbm_mma_workspace_size(self.n, self.m, byref(size)), "lbm_mma_workspace_size")
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        h = c_void_p()
+        check(lib().lbm_mma_create(self.n, self.m, _ptr(xmin), _ptr(xmax), self.workspace.data_ptr(), size.value,
+                                   c_void_p(self.stream.cuda_stream), byref(h)), "lbm_mma_create")
+        self.h = h
+
+    def update(self, x, fval, dfdx):
+        """One iteration; returns the subproblem's multipliers."""
+        import torch
+
+        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == self.n
+        fv = np.ascontiguousarray(fval, dtype=np.float64).reshape(-1)
+        assert fv.size == self.m + 1
+        df = torch.as_tensor(dfdx, dtype=torch.float64, device=self.device).contiguous()
+        assert df.numel() == (self.m + 1) * self.n
+        lam = (c_double * self.m)()
+        check(lib().lbm_mma_update(self.h, x.data_ptr(), _ptr(fv), df.data_ptr(), lam), "lbm_mma_update")
+        return np.array(lam[:])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_mma_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbmadj.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_FILES = ("lbmadj.cu", "noalloc.cu")
+CU_FILES = ("lbmadj.cu", "noalloc.cu", "mma.cu")
 
 
 def _sources():

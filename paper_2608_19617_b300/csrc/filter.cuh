@@ -102,4 +102,30 @@ __global__ void filter_adjoint_gather_kernel(const double* __restrict__ g, const
   }
 }
 
+// Volume fraction of Sec. 3.3, V = (1/n_D) sum_{i in D} (1 - phi_i) = mean gamma
+// over the design box: per-block sums of gamma (FP64) over the box nodes,
+// added by the host in block order.
+constexpr int kVolThreads = 256;
+__global__ void __launch_bounds__(kVolThreads) design_volume_kernel(const float* __restrict__ gamma, int nx, int ny,
+                                                                    int x0, int x1, int y0, int y1, int z0, int z1,
+                                                                    double* __restrict__ part) {
+  const long long bx = x1 - x0, by = y1 - y0, cells = bx * by * (long long)(z1 - z0);
+  double s = 0.0;
+  for (long long k = blockIdx.x * (long long)kVolThreads + threadIdx.x; k < cells;
+       k += (long long)gridDim.x * kVolThreads) {
+    const long long X = x0 + k % bx, Y = y0 + (k / bx) % by, Z = z0 + k / (bx * by);
+    s += double(gamma[X + nx * (Y + (long long)ny * Z)]);
+  }
+  __shared__ double w[kVolThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kVolThreads / 32; ++k) t += w[k];
+    part[blockIdx.x] = t;
+  }
+}
+
 }  // namespace lbm

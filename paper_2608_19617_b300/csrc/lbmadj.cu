@@ -1534,6 +1534,45 @@ lbm_status lbm_design_gradient_filtered(lbm_ctx* c, double* grad, size_t n) {
   return LBM_OK;
 }
 
+lbm_status lbm_filter_chain_rule(lbm_ctx* c, const double* dgamma, double* dx, size_t n) {
+  if (!c || !dgamma || !dx) return fail(LBM_ERR_ARG, "null argument");
+  if (!c->filtered) return fail(LBM_ERR_STATE, "the design was not set through lbm_set_design_filtered");
+  if (n != c->n) return fail(LBM_ERR_ARG, "sensitivity length %zu, expected %zu", n, c->n);
+  double* t = c->at<double>(c->lay.stage);   // the stage holds Q N >= 3 N doubles
+  double* out = t + c->n;
+  double* g = t + 2 * c->n;
+  CUDA_TRY(cudaMemcpyAsync(g, dgamma, n * 8, cudaMemcpyDefault, c->stream));
+  const long long blocks = (long long)(c->n + 255) / 256;
+  const int nb = int(blocks < 148 * 32 ? blocks : 148 * 32);
+  lbm::filter_adjoint_scale_kernel<<<nb, 256, 0, c->stream>>>(g, c->at<double>(c->lay.xfilt),
+                                                               c->at<double>(c->lay.wfilt), t, c->fgeo);
+  lbm::filter_adjoint_gather_kernel<<<nb, 256, 0, c->stream>>>(g, t, out, c->fgeo);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(dx, out, n * 8, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_design_volume(lbm_ctx* c, double* volume) {
+  if (!c || !volume) return fail(LBM_ERR_ARG, "null argument");
+  const int* d = c->cfg.design_box;
+  const long long cells = (long long)(d[1] - d[0]) * (d[3] - d[2]) * (d[5] - d[4]);
+  if (cells <= 0) return fail(LBM_ERR_ARG, "the design box is empty");
+  const long long want = (cells + lbm::kVolThreads - 1) / lbm::kVolThreads;
+  const int nb = int(want < 148 * 4 ? want : 148 * 4);
+  double* part = c->at<double>(c->lay.stage);
+  lbm::design_volume_kernel<<<nb, lbm::kVolThreads, 0, c->stream>>>(
+      c->at<float>(c->lay.gamma), c->cfg.nx, c->cfg.ny, d[0], d[1], d[2], d[3], d[4], d[5], part);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> h(nb);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), part, size_t(nb) * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += h[b];
+  *volume = s / double(cells);
+  return LBM_OK;
+}
+
 lbm_status lbm_get_state(lbm_ctx* c, double* f, size_t n) {
   if (!c || !f) return fail(LBM_ERR_ARG, "null argument");
   if (n != c->n * c->q) return fail(LBM_ERR_ARG, "state length %zu, expected %zu", n, c->n * c->q);

@@ -284,9 +284,11 @@ def config_cylinder(re=51.2) -> Case:
     radius 8 at the domain centre with phi = 0.5 inside (gamma = 0.5), Re = 51.2
     on the diameter by default (vortex shedding), uniform inlet u = 0.04 (the
     paper gives no inlet speed), Zou-He pressure outlet, walls y = 0 and 99;
-    objective = the drag force over the design domain, the 32x32 square around
-    the cylinder; windows of 5000 steps sampled every 50 (Delta W), checkpoints
-    every 100, tolerance 1e-3 on the drag monitor."""
+    objective = the drag on the body over the design domain, the 32x32 square
+    around the cylinder: weights -1 on Eq. 44's F_x, the x-momentum the
+    partial bounce-back gives the fluid (negative for flow in +x), so that
+    minimising J reduces the drag; windows of 5000 steps sampled every 50
+    (Delta W), checkpoints every 100, tolerance 1e-3 on the drag monitor."""
     nx, ny = 200, 100
     cls = channel_classes(nx, ny, outlet=OUTLET_P)
     gamma = np.where(disk_mask(nx, ny, 100, 50, 16), 0.5, 0.0)[None]
@@ -295,7 +297,7 @@ def config_cylinder(re=51.2) -> Case:
     uin[0, 0] = uin[0, ny - 1] = 0.0
     box = (84, 116, 34, 66)
     w = np.zeros((1, ny, nx))
-    w[0, box[2]:box[3], box[0]:box[1]] = 1.0
+    w[0, box[2]:box[3], box[0]:box[1]] = -1.0
     return Case(name="cylinder200x100", lattice=9, nx=nx, ny=ny, nz=1,
                 tau=tau_from_re(0.04, 16, re), cs_smag=0.1, node_class=cls, gamma=gamma,
                 inlet_u=uin, obj_weights=w, obj_kind=OBJ_DRAG, monitor_kind=MON_DRAG,

@@ -170,3 +170,23 @@ def test_create_rejects_a_missing_workspace(lib):
 def test_pressure_outlet_is_d2q9_only(lib):
     case = I.small_duct3d(8, 5, 5, outlet=I.OUTLET_P)
     assert _create(case) == B.LBM_ERR_ARG
+
+
+def test_mma_workspace_size_and_arguments_on_the_host(lib):
+    """lbm_mma_workspace_size validates n and m before any CUDA call, and
+    grows with n and m (the approximation coefficients are [m+1][n] each);
+    lbm_mma_create rejects null pointers the same way."""
+    size = ctypes.c_size_t()
+    for n, m in ((0, 1), (10, 0), (10, B.LBM_MMA_MAX_M + 1)):
+        assert lib.lbm_mma_workspace_size(n, m, ctypes.byref(size)) == B.LBM_ERR_ARG
+    sizes = {}
+    for n, m in ((1000, 1), (1000, 2), (2000, 2)):
+        assert lib.lbm_mma_workspace_size(n, m, ctypes.byref(size)) == B.LBM_OK
+        assert size.value % 256 == 0
+        sizes[n, m] = size.value
+    # per variable: 8 vectors of n doubles + p and q for every function (each region rounded to 256 bytes)
+    assert abs((sizes[1000, 2] - sizes[1000, 1]) - 2 * 1000 * 8) <= 2 * 256
+    assert abs((sizes[2000, 2] - sizes[1000, 2]) - (8 + 2 * 3) * 1000 * 8) <= 10 * 256
+    h = ctypes.c_void_p()
+    assert lib.lbm_mma_create(10, 1, None, None, None, 0, None, ctypes.byref(h)) == B.LBM_ERR_ARG
+    assert lib.lbm_mma_update(None, None, None, None, None) == B.LBM_ERR_ARG

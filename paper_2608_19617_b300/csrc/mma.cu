@@ -331,6 +331,17 @@ bool solve_neg_def(int k, double A[LBM_MMA_MAX_M][LBM_MMA_MAX_M], const double* 
   return true;
 }
 
+// The kernels read x and dfdx directly: accept device (or managed) memory only,
+// so that a host pointer is an argument error rather than a device fault.
+bool on_device(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" {
@@ -386,6 +397,7 @@ lbm_status lbm_mma_create(size_t n, int32_t m, const double* xmin, const double*
 
 lbm_status lbm_mma_update(lbm_mma* o, double* x, const double* fval, const double* dfdx, double* lam_out) {
   if (!o || !x || !fval || !dfdx) return mma_fail(LBM_ERR_ARG, "null argument");
+  if (!on_device(x) || !on_device(dfdx)) return mma_fail(LBM_ERR_ARG, "x and dfdx must be device memory");
   const int m = o->dev.m;
   for (int i = 0; i <= m; ++i)
     if (!std::isfinite(fval[i])) return mma_fail(LBM_ERR_ARG, "fval[%d] is not finite", i);

@@ -104,6 +104,25 @@ def test_mma_arguments():
     assert e.value.status == B.LBM_ERR_ARG
 
 
+def test_mma_update_rejects_host_pointers():
+    """x and dfdx are read by the kernels: host memory is an argument error,
+    caught on the host before any launch."""
+    import torch
+    n = 64
+    gpu = B.Mma(np.zeros(n), np.ones(n), 1)
+    f = np.zeros(2)
+    x_host, df_host = np.full(n, 0.5), np.zeros((2, n))
+    assert B.lib().lbm_mma_update(gpu.h, x_host.ctypes.data, f.ctypes.data, df_host.ctypes.data, None) == B.LBM_ERR_ARG
+    x = torch.full((n,), 0.5, dtype=torch.float64, device="cuda")
+    assert B.lib().lbm_mma_update(gpu.h, x.data_ptr(), f.ctypes.data, df_host.ctypes.data, None) == B.LBM_ERR_ARG
+    df = torch.zeros((2, n), dtype=torch.float64, device="cuda")
+    df[0] = 1.0
+    df[1] = 1.0 / n
+    gpu.update(x, np.array([0.0, -0.1]), df)          # a valid call still works afterwards
+    assert torch.all(x < 0.5)
+    gpu.close()
+
+
 def test_design_volume_and_filter_chain_rule_match_the_oracle():
     case = f32_inputs(I.small_channel(150, 12, window_len=12, outlet=I.OUTLET_P, tau=0.53))
     shape = (case.nz, case.ny, case.nx)

@@ -409,7 +409,7 @@ lbm_status lbm_mma_create(size_t n, int32_t m, const double* xmin, const double*
  *   dfdx     device, double [m+1][n]: the gradients, objective first
  *   lam_out  host, double [m] or NULL: the subproblem's multipliers
  * Synchronises the stream.  Errors: LBM_ERR_ARG (null pointers, non-finite
- * fval), LBM_ERR_CUDA. */
+ * fval, x or dfdx not device memory), LBM_ERR_CUDA. */
 lbm_status lbm_mma_update(lbm_mma* mma, double* x, const double* fval, const double* dfdx, double* lam_out);
 
 lbm_status lbm_mma_destroy(lbm_mma* mma);

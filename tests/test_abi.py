@@ -190,3 +190,21 @@ def test_mma_workspace_size_and_arguments_on_the_host(lib):
     h = ctypes.c_void_p()
     assert lib.lbm_mma_create(10, 1, None, None, None, 0, None, ctypes.byref(h)) == B.LBM_ERR_ARG
     assert lib.lbm_mma_update(None, None, None, None, None) == B.LBM_ERR_ARG
+
+
+def test_every_workload_is_a_valid_configuration(lib):
+    """Each shipped workload passes the host-side validation of lbm_workspace_size
+    (FP32, and FP64 with native checkpoints); the full-time form of the cylinder
+    case (a 60000-step window kept whole, K = 1) sizes to its complete history."""
+    for name, make in I.WORKLOADS.items():
+        case = make()
+        n = B.workspace_size(B.config_from_case(case, B.LBM_FP32, pipeline=1))
+        assert n > case.n * case.lattice * 4 * 2, name
+        n64 = B.workspace_size(B.config_from_case(case.replace(ckpt_format=I.CKPT_NATIVE), B.LBM_FP64))
+        assert n64 > 0, name
+    cyl = I.WORKLOADS["cylinder200x100"]()
+    T = 12 * cyl.window_len
+    full = cyl.replace(window_len=T, ckpt_every=1, sample_from=T - cyl.window_len)
+    size = B.workspace_size(B.config_from_case(full, B.LBM_FP32, pipeline=1))
+    history = T * cyl.n * cyl.lattice * 4
+    assert history <= size <= history * 1.01 + (1 << 28)

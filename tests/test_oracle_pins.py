@@ -293,6 +293,61 @@ def test_poiseuille_profile():
     assert abs(dpdx / (-8 * nu * 0.02 / (ny - 1) ** 2) - 1) < 0.03
 
 
+@pytest.mark.parametrize("q", [9, 19])
+def test_objectives_on_a_uniform_stream(q):
+    """Closed forms of the four objective integrands (R10) on a uniform stream
+    rho = 1, u = u0 e_x through a uniform partial solid: the equilibrium is
+    its own collision (Pi^neq = 0), so
+      drag (Eq. 44)      sum_a c_xa g (h_abar - h_a) = -2 g rho u0,
+      velocity deviation |u - u_ref|^2 = (u0 - u_ref)^2,
+      pressure           cs^2 rho = 1/3,
+      dissipation        0."""
+    u0, uref, g0 = 0.03, 0.01, 0.3
+    nx, ny, nz = 7, 5, (4 if q == 19 else 1)
+    case = I.periodic_box(nx, ny, nz, lattice=q, gamma=np.full((nz, ny, nx), g0))
+    case = case.replace(obj_uref=(uref, 0.0, 0.0))
+    pr = O.Problem(case)
+    u = np.zeros((pr.lat.d, pr.n))
+    u[0] = u0
+    p0 = O.equilibrium(pr.lat, np.ones(pr.n), u)
+    g = pr.g()
+    f, h, _, aux = pr.step(p0, g)
+    want = {I.OBJ_DRAG: -2.0 * g * u0, I.OBJ_VELOCITY_DEV: np.full(pr.n, (u0 - uref) ** 2),
+            I.OBJ_PRESSURE: np.full(pr.n, 1.0 / 3.0), I.OBJ_DISSIPATION: np.zeros(pr.n)}
+    for kind, w in want.items():
+        prk = O.Problem(case.replace(obj_kind=kind))
+        got = prk.local_objective(f, h, aux, g)
+        assert np.allclose(got, w, rtol=1e-12, atol=1e-15), kind
+
+
+def test_dissipation_objective_is_the_poiseuille_dissipation():
+    """In developed Poiseuille flow (Cs = 0, so nu_eff = nu) the dissipation
+    integrand equals 2 rho nu S:S = rho nu (du/dy)^2 of the analytic parabola
+    u = 4 u_max y (H - y) / H^2 at the mid-channel nodes, to the scheme's
+    second-order accuracy."""
+    nx, ny, tau, umax = 48, 17, 0.8, 0.02
+    case = I.small_channel(nx, ny, tau=tau, cs_smag=0.0, u_in=umax, profile="parabolic",
+                           outlet=I.OUTLET_P, noise_amp=0.0, obj_kind=I.OBJ_DISSIPATION)
+    gamma = np.zeros((1, ny, nx))
+    gamma[case.node_class == I.WALL] = 1.0
+    case = case.replace(gamma=gamma)
+    pr = O.Problem(case)
+    p = pr.initial_state()
+    g = pr.g()
+    for _ in range(4000):
+        f, h, p, aux = pr.step(p, g)
+    psi = pr.local_objective(f, h, aux, g).reshape(ny, nx)[:, nx // 2]
+    H = ny - 1
+    y = np.arange(ny)
+    nu = (tau - 0.5) / 3.0
+    want = nu * (4 * umax * (H - 2 * y) / H ** 2) ** 2
+    inner = slice(2, ny - 2)                        # away from the wall rows and their neighbours
+    # 2%: the developed profile itself is within 0.5% of the parabola at H = 16 (test_poiseuille_profile), and
+    # (du/dy)^2 doubles that; a dropped factor of the integrand (2, tau_eff, rho) would be off by 50-100%
+    assert np.abs(psi[inner] - want[inner]).max() <= 0.02 * want[inner].max()
+    assert abs(psi[inner].sum() / want[inner].sum() - 1) < 0.02
+
+
 def test_mirror_symmetry():
     """A y-symmetric channel stays symmetric: rho even, u_x even, u_y odd."""
     nx, ny = 20, 11

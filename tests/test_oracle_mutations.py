@@ -110,3 +110,47 @@ def test_dropped_cs2_delta_in_regularization_is_caught():
     wrong = lat.w[:, None] / (2 * O.CS4) * np.einsum("ap,aq,pqn->an", lat.c, lat.c, aux["pi"])
     assert np.abs(wrong.sum(0)).max() > 1e-4
     assert np.abs(aux["hneq"].sum(0)).max() < 1e-15
+
+
+def _closed_form_gap(q=9, window_len=12, sample_every=3, sample_from=3):
+    from _util import decaying_stream_window
+    J, M, J_want, M_want = decaying_stream_window(q, window_len, sample_every, sample_from)
+    return max(abs(J - J_want) / abs(J_want), abs(M - M_want) / abs(M_want))
+
+
+def test_unmutated_closed_form_gap_is_rounding():
+    assert _closed_form_gap() < 1e-13
+
+
+def test_dropped_half_in_drag_coefficient_is_caught(monkeypatch):
+    """Eq. 25 without the 1/2 of the dynamic pressure."""
+    def mutant(self, f, h, aux, g):
+        j = (self.w_obj * self.local_objective(f, h, aux, g)).sum()
+        c = self.case
+        return j, self.drag_density(h, g).sum() / (c.rho_out * c.monitor_u ** 2 * c.monitor_l)
+
+    monkeypatch.setattr(O.Problem, "sample", mutant)
+    assert _closed_form_gap() > 0.1
+
+
+def test_weight_ignoring_the_first_sampled_step_is_caught(monkeypatch):
+    """Eq. 42 weight dW/|W| instead of dW over the sampled span."""
+    monkeypatch.setattr(O.Problem, "sample_weight",
+                        lambda self: int(self.case.sample_every) / int(self.case.window_len))
+    assert _closed_form_gap() > 0.1
+
+
+def test_sampling_every_step_is_caught(monkeypatch):
+    """Samples at every step of the span instead of every dW-th step."""
+    monkeypatch.setattr(O.Problem, "sampled", lambda self, k: k >= int(self.case.sample_from))
+    assert _closed_form_gap() > 1e-3
+
+
+def test_shifted_sampling_instants_are_caught(monkeypatch):
+    """Samples one step late (k = s0 + 1, s0 + 1 + dW, ...)."""
+    def mutant(self, k):
+        s0, dw = int(self.case.sample_from), int(self.case.sample_every)
+        return k > s0 and (k - s0 - 1) % dw == 0
+
+    monkeypatch.setattr(O.Problem, "sampled", mutant)
+    assert _closed_form_gap() > 1e-3

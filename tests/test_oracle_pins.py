@@ -469,3 +469,17 @@ def test_uniform_flow_is_a_fixed_point_of_inlet_and_outlet(q, outlet):
         _, _, p2, _ = pr.step(p, g)
         np.testing.assert_allclose(p2, p, atol=3e-17)
         p = p2
+
+
+@pytest.mark.parametrize("q", [9, 19])
+@pytest.mark.parametrize("window_len,sample_every,sample_from", [(12, 1, 0), (12, 3, 0), (12, 3, 3), (20, 4, 8)])
+def test_window_means_and_drag_coefficient_in_closed_form(q, window_len, sample_every, sample_from):
+    """Eq. 25 (C_d = F_x / (1/2 rho_0 U^2 L)) and the window means of Eq. 42
+    (samples every dW-th step from the first sampled step, weight dW over the
+    sampled span) on a decaying uniform stream whose every sample is known in
+    closed form.  A dropped 1/2, a squared L, a wrong sample count or shifted
+    sampling instants each change the result by far more than rounding."""
+    from _util import decaying_stream_window
+    J, M, J_want, M_want = decaying_stream_window(q, window_len, sample_every, sample_from)
+    assert abs(J - J_want) <= 1e-13 * abs(J_want), (J, J_want)
+    assert abs(M - M_want) <= 1e-13 * abs(M_want), (M, M_want)

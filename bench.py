@@ -61,10 +61,6 @@ def parse():
     ap.add_argument("--pipeline", type=int, default=1,
                     help="recompute the next segment while the adjoint sweeps the current one")
     ap.add_argument("--pdl", type=int, default=1, help="programmatic dependent launch of the step kernels")
-    ap.add_argument("--tma", type=int, default=0,
-                    help="stage the interior forward steps' source rows in shared memory with TMA copies")
-    ap.add_argument("--flow", type=int, default=0,
-                    help="persistent launches: one cooperative kernel per checkpoint segment")
     ap.add_argument("--quick", action="store_true",
                     help="profiling run: no CPU baseline, no FP64 check, no e2e pass")
     ap.add_argument("--full-time", action="store_true",
@@ -338,10 +334,6 @@ def run_ours(args, case, rank, world, local):
         sol = B.Solver(case, prec, stream=stream, pipeline=int(args.pipeline))
     sol.set_graphs(bool(args.graphs))
     sol.set_pdl(bool(args.pdl))
-    if args.flow:
-        sol.set_flow(True)
-    if args.tma:
-        sol.set_tma(True)
     n = case.n
     W, K = case.window_len, case.ckpt_every
     grad_dev = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -433,9 +425,8 @@ def run_ours(args, case, rank, world, local):
     # and adjoint steps may run concurrently.
     sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / len(sweep_ev)
     sweep_b = (bytes_per_lu(case, "adjoint", rs=rs) + bytes_per_lu(case, "recompute", rs=rs) * (K - 1) / K) * n
-    fk = ("fwd_flow_kernel" if args.flow else
-          ("fwd_tma_kernel+" if args.tma else "fwd_interior_kernel+") + fwd_face_kernel(case))
-    ak = "adj_flow_kernel" if args.flow else "adj_interior_kernel+adj_face_kernel"
+    fk = "fwd_interior_kernel+" + fwd_face_kernel(case)
+    ak = "adj_interior_kernel+adj_face_kernel"
     units = {
         "forward step": {"bytes": bytes_per_lu(case, "forward", rs=rs) * n,
                          "us": phase_rows["forward"]["avg_step_us"], "kernel": fk,
@@ -482,11 +473,6 @@ def run_ours(args, case, rank, world, local):
         with torch.cuda.stream(stream):
             s32 = B.Solver(c32, B.LBM_FP32, stream=stream) if sol.ctx is None else sol
             ref = B.Solver(c64, B.LBM_FP64, stream=stream)
-        if args.flow:
-            s32.set_flow(True)
-            ref.set_flow(True)
-        if args.tma:
-            s32.set_tma(True)
         s32.set_state(p)
         J32, _ = s32.step_window()
         s32.adjoint_window()
@@ -528,9 +514,8 @@ def run_ours(args, case, rank, world, local):
                    "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
                    "ckpt_format": CKPT_NAMES[case.ckpt_format], "tau": case.tau,
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
-                   "cuda_graphs": bool(args.graphs), "pipeline": bool(args.pipeline) and not args.flow,
-                   "pdl": bool(args.pdl), "tma_staging": bool(args.tma), "persistent": bool(args.flow),
-                   "persistent_bands": sched["flow_bands"] if args.flow else None,
+                   "cuda_graphs": bool(args.graphs), "pipeline": bool(args.pipeline),
+                   "pdl": bool(args.pdl),
                    "l2": "flushed (256 MB write) before every timed step; inside a step the forward "
                          "lattices (19 MB) stay L2-resident"},
         "fwd_mlups": 1e-6 * timing["forward"]["lattice_updates"] / (timing["forward"]["ms"] / 1e3),

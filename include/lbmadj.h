@@ -182,7 +182,9 @@ lbm_status lbm_window_converged(lbm_ctx* ctx, int* converged, double* ratio);
 lbm_status lbm_adjoint_window(lbm_ctx* ctx, double* J_eff);
 
 /* dJ_eff/dgamma of the last adjoint window into grad (host or device, FP64
- * [N]); zero outside design_box.  n must equal N.
+ * [N]): the sensitivity of Eq. 40, sum over the window's steps of the adjoint
+ * times dp/dphi = g'(phi) (h_abar - h_a), with the sign flipped for
+ * gamma = 1 - phi; zero outside design_box.  n must equal N.
  * Errors: LBM_ERR_STATE before lbm_adjoint_window, LBM_ERR_ARG for n != N. */
 lbm_status lbm_design_gradient(lbm_ctx* ctx, double* grad, size_t n);
 
@@ -275,33 +277,6 @@ lbm_status lbm_set_pdl(lbm_ctx* ctx, int32_t enable);
  * Synchronises both streams; launched directly, not as a replayed graph. */
 lbm_status lbm_step_window_along(lbm_ctx* ctx, lbm_ctx* ref, double* J_window, double* monitor_window);
 
-/* Run each checkpoint segment of the forward window, of the recompute and of
- * the adjoint sweep as ONE persistent launch (1) instead of one launch per
- * step (0, the default).  The persistent kernels (a library design with no
- * counterpart in the paper) cut the lattice into bands of consecutive nodes,
- * one block per band, all blocks co-resident (cooperative launch); a block
- * starts step k once the bands its step reads from or writes over have
- * finished step k-1.  Nodes are computed by the same explicitly rounded
- * arithmetic as in the per-step kernels, so states, adjoint fields and
- * gradients are theirs; window sums are added in another order.
- * The adjoint sweep then runs serially (cfg.pipeline is ignored).  Every wait
- * is bounded (4 s without progress): a wait that runs out makes the window or
- * sweep fail with LBM_ERR_CUDA instead of hanging.  Fails with LBM_ERR_ARG
- * where the schedule does not exist: D2Q9 batches (nz > 1) or a device
- * without cooperative launch. */
-lbm_status lbm_set_flow(lbm_ctx* ctx, int32_t enable);
-
-/* Stage the source rows of the interior forward steps (window and recompute)
- * in shared memory with TMA bulk-tensor copies, several tiles ahead of the
- * tile being computed (1), or load them straight into registers (0, the
- * default).  The node arithmetic is the same explicitly rounded code and the
- * block sums land in the same slots, so results are those of the register
- * path.  Needs interior nodes and a row pitch
- * (nx * element size) that is a multiple of 16 bytes: LBM_ERR_ARG otherwise.
- * Copy waits are bounded; one that runs out fails the window or sweep with
- * LBM_ERR_CUDA. */
-lbm_status lbm_set_tma(lbm_ctx* ctx, int32_t enable);
-
 /* First sampled step of each following window: the objective and monitor
  * means (Eq. 42) and the adjoint's objective sources use the steps first,
  * first + sample_every, ... < window_len, weighted by
@@ -319,21 +294,10 @@ lbm_status lbm_set_tma(lbm_ctx* ctx, int32_t enable);
  * entry point always samples from step 0. */
 lbm_status lbm_set_sample_start(lbm_ctx* ctx, int32_t first);
 
-/* Test hook of the persistent kernels' bounded waits: the longest wait without
- * progress (seconds, default 4) and one band that computes but never
- * publishes its progress (-1, the default: none), so that its neighbours'
- * waits run out and the window or sweep fails with LBM_ERR_CUDA while the
- * context stays usable.  Not for production use. */
-lbm_status lbm_set_flow_test_hook(lbm_ctx* ctx, double wait_seconds, int32_t silent_band);
-
 /* How the context launches its work. */
 typedef struct {
-  int32_t flow_bands;       /* bands of the persistent schedule (0: unavailable)       */
-  int32_t flow;             /* 1: persistent segment launches (lbm_set_flow)          */
   int32_t graphs;           /* 1: windows and sweeps replay as CUDA graphs            */
   int32_t pdl;              /* 1: programmatic dependent launch                       */
-  int32_t tma_available;    /* 1: lbm_set_tma(ctx, 1) is accepted                     */
-  int32_t tma;              /* 1: TMA-staged interior forward steps (lbm_set_tma)     */
   int64_t kernels_window;   /* kernels enqueued by the last window (0 before one)     */
   int64_t kernels_adjoint;  /* kernels enqueued by the last adjoint sweep             */
 } lbm_schedule;

@@ -48,8 +48,7 @@ class LbmFilter(ctypes.Structure):
 
 
 class LbmSchedule(ctypes.Structure):
-    _fields_ = [("flow_bands", c_int32), ("flow", c_int32), ("graphs", c_int32), ("pdl", c_int32),
-                ("tma_available", c_int32), ("tma", c_int32),
+    _fields_ = [("graphs", c_int32), ("pdl", c_int32),
                 ("kernels_window", c_int64), ("kernels_adjoint", c_int64)]
 
 
@@ -94,8 +93,6 @@ def lib() -> ctypes.CDLL:
         "lbm_get_counters": (st, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
         "lbm_set_graphs": (st, [c_void_p, c_int32]),
         "lbm_set_pdl": (st, [c_void_p, c_int32]),
-        "lbm_set_flow": (st, [c_void_p, c_int32]),
-        "lbm_set_tma": (st, [c_void_p, c_int32]),
         "lbm_set_sample_start": (st, [c_void_p, c_int32]),
         "lbm_filter_chain_rule": (st, [c_void_p, c_void_p, c_void_p, c_size_t]),
         "lbm_design_volume": (st, [c_void_p, POINTER(c_double)]),
@@ -105,7 +102,6 @@ def lib() -> ctypes.CDLL:
         "lbm_mma_update": (st, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
         "lbm_mma_destroy": (st, [c_void_p]),
         "lbm_get_schedule": (st, [c_void_p, POINTER(LbmSchedule)]),
-        "lbm_set_flow_test_hook": (st, [c_void_p, c_double, c_int32]),
         "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_status_string": (ctypes.c_char_p, [c_int32]),
@@ -296,14 +292,6 @@ class Solver:
     def set_pdl(self, enable: bool):
         check(lib().lbm_set_pdl(self.ctx, int(bool(enable))), "lbm_set_pdl")
 
-    def set_flow(self, enable: bool):
-        """Persistent segment launches (lbm_set_flow)."""
-        check(lib().lbm_set_flow(self.ctx, int(bool(enable))), "lbm_set_flow")
-
-    def set_tma(self, enable: bool):
-        """TMA-staged interior forward steps (lbm_set_tma)."""
-        check(lib().lbm_set_tma(self.ctx, int(bool(enable))), "lbm_set_tma")
-
     def filter_chain_rule(self, dgamma, out=None):
         """(d gamma / d x)^T dgamma through the filter and projection (lbm_filter_chain_rule)."""
         dg = np.ascontiguousarray(dgamma, dtype=np.float64).reshape(-1)
@@ -321,11 +309,6 @@ class Solver:
         """First sampled step of each following window (lbm_set_sample_start);
         a full-time run of T steps samples from T - |W|."""
         check(lib().lbm_set_sample_start(self.ctx, int(first)), "lbm_set_sample_start")
-
-    def set_flow_test_hook(self, wait_seconds: float = 4.0, silent_band: int = -1):
-        """Bounded-wait test hook of the persistent kernels (lbm_set_flow_test_hook)."""
-        check(lib().lbm_set_flow_test_hook(self.ctx, float(wait_seconds), int(silent_band)),
-              "lbm_set_flow_test_hook")
 
     def schedule(self) -> dict:
         """Launch configuration and kernels per window / adjoint sweep (lbm_get_schedule)."""

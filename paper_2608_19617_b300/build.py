@@ -37,7 +37,14 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def _compile_cmd(src, obj, extra=()):
+    return [nvcc_path(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3",
+            "-I", INCLUDE, "-I", CSRC, *extra, "-c", src, "-o", obj]
+
+
 def command(out=LIB, extra=()):
+    """One nvcc invocation that compiles and links every source (for reference;
+    build() compiles the files in parallel and links them)."""
     return [nvcc_path(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3",
             "--shared", "-cudart", "shared", "-I", INCLUDE, "-I", CSRC, *extra,
             *[os.path.join(CSRC, f) for f in CU_FILES], "-o", out]
@@ -49,14 +56,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(s) <= t for s in srcs):
             return LIB
-    cmd = command()
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    procs = []
+    for f in CU_FILES:
+        obj = os.path.join(objdir, f + ".o")
+        cmd = _compile_cmd(os.path.join(CSRC, f), obj)
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((cmd, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    objs = []
+    for cmd, obj, p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + out + err)
+        objs.append(obj)
     tmp = LIB + ".tmp"
-    cmd[-1] = tmp
-    res = subprocess.run(cmd, capture_output=True, text=True)
+    link = [nvcc_path(), *ARCH, "--shared", "-cudart", "shared", *objs, "-o", tmp]
+    if verbose:
+        print(" ".join(link), file=sys.stderr)
+    res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
+        raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
     os.replace(tmp, LIB)
     return LIB
 

@@ -79,7 +79,6 @@ struct alignas(32) Sums {
 struct WindowAcc {
   double jmean, mmean, mprev, ratio;
   int has_prev, converged, nonfinite;
-  int stalled;   // a persistent step kernel gave up waiting (flags[2])
 };
 
 template <class T>
@@ -95,6 +94,12 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 #endif
+}
+
+// Is step `step` of a window a sampling instant: every dW-th step from the
+// first sampled step s0 on (Eq. 42; s0 > 0 only for the full-time run).
+__host__ __device__ __forceinline__ bool sampled_step(int step, int s0, int dW) {
+  return dW > 0 && step >= s0 && (step - s0) % dW == 0;
 }
 
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
@@ -119,8 +124,8 @@ __device__ __forceinline__ bool neighbour(const Geo& g, int x, int y, int z, int
 // samples) is written with them, in a
 // fixed order, wherever a product meets a sum: the compiler then has no
 // contraction left to choose, and every kernel that inlines it (interior,
-// face, TMA-staged, persistent, the step that writes a moment checkpoint, the
-// checkpoint decoder) computes the same bits.
+// face, the step that writes a moment checkpoint, the checkpoint decoder)
+// computes the same bits.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -483,15 +488,7 @@ __device__ __forceinline__ R local_objective(const Mom<L, R>& M, const Obj<R>& o
   }
 }
 
-// Load of a field that other blocks of the same launch write (persistent step
-// kernels): through L2, never from a possibly stale L1 or read-only cache line.
-template <bool CG, class R>
-__device__ __forceinline__ R ldf(const R* p) {
-  if constexpr (CG) return __ldcg(p);
-  else return *p;
-}
-
-// The per-step fields of a step (persistent kernels change them every step).
+// The per-step fields of a step.
 template <class R>
 struct FwdStep {
   const R* src;   // p^{n-1}
@@ -578,8 +575,7 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
 // One node of a forward step (interior or face node): pull (Eq. 7), complete
 // the boundary populations of a face node (Eqs. 19-21), then forward_core.
 // For a face node k is its row in the face table; for an interior node k is unused.
-// CG: the source field is written concurrently by other blocks of the launch.
-template <class L, class R, bool FACE, bool CG = false, bool MOM = false>
+template <class L, class R, bool FACE, bool MOM = false>
 __device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<R>& P, int x, int y, int z,
                                              unsigned i, unsigned k, R& bj, R& bm) {
   const Geo& g = A.geo;
@@ -588,12 +584,12 @@ __device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<
   if (FACE) {
     const FaceTable& t = A.ft;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = ldf<CG>(src + (a * g.n + t.src[a * t.n + k]));
+    for (int a = 0; a < L::Q; ++a) f[a] = src[a * g.n + t.src[a * t.n + k]];
     const unsigned info = t.info[k];
     apply_rules<L, R>(f, info & 0xffffffu, uint8_t(info >> 24), R(t.u0[k]), A.ph.rho_out);
   } else {
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = ldf<CG>(src + (a * g.n + i - offset<L>(g, a)));
+    for (int a = 0; a < L::Q; ++a) f[a] = src[a * g.n + i - offset<L>(g, a)];
   }
   forward_core<L, R, MOM>(A, P, x, y, z, i, f, bj, bm);
 }
@@ -611,7 +607,7 @@ __global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
   if (A.sample) sample_fetch(&sums, A.blk, bid);   // uniform across the grid
   R bj = 0, bm = 0;
   if (x < g.nx - 1)
-    forward_node<L, R, false, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
+    forward_node<L, R, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
   if (A.sample) {
     block_sum2<R>(bj, bm);
     sample_commit_fetched(double(bj), double(bm), &sums, A.blk, bid);
@@ -630,7 +626,7 @@ __global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned
   const unsigned i = k < A.ft.n ? A.ft.idx[k] : kNone;   // rows padded per slice hold kNone
   if (i != kNone) {
     const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
-    forward_node<L, R, true, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, k, bj, bm);
+    forward_node<L, R, true, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, k, bj, bm);
   }
   if (A.sample) {
     block_sum2<R>(bj, bm);
@@ -768,25 +764,22 @@ __global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, in
   acc->mprev = mm;
   acc->has_prev = 1;
   acc->nonfinite = nonfinite[0];
-  acc->stalled = nonfinite[2];
 }
 
 // Per-slice window means of a batch of independent 2D lattices (D2Q9, nz > 1):
 // one block per slice sums the block sums of that slice's interior blocks
-// (bz == slice) and face blocks (slice-aligned) in a fixed order.  With
-// nflat > 0 (a single lattice, nz == 1) the one slice sums blk[0 .. nflat).
-// Runs before window_end_kernel, which clears the block sums.
+// (bz == slice) and face blocks (slice-aligned) in a fixed order.  Runs
+// before window_end_kernel, which clears the block sums.
 __global__ void __launch_bounds__(kEndThreads) slice_end_kernel(const double* blk, int igx, int igy, int fbs,
                                                                 int nint, double nsamples, const double* jconst,
-                                                                double mon_scale, int mon_kind, double* out,
-                                                                int nflat) {
+                                                                double mon_scale, int mon_kind, double* out) {
   __shared__ double sh[4][kEndThreads];
   const int slice = blockIdx.x, t = threadIdx.x;
   const int nib = igx * igy;              // interior blocks of one slice
-  const int count = nflat > 0 ? nflat : nib + fbs;
+  const int count = nib + fbs;
   double sj = 0, cj = 0, sm = 0, cm = 0;
   for (int b = t; b < count; b += kEndThreads) {
-    const int bid = nflat > 0 ? b : b < nib ? slice * nib + b : nint + slice * fbs + (b - nib);
+    const int bid = b < nib ? slice * nib + b : nint + slice * fbs + (b - nib);
     const Sums a = reinterpret_cast<const Sums*>(blk)[bid];
     neumaier(sj, cj, a.x);
     neumaier(sj, cj, a.y);
@@ -946,8 +939,7 @@ struct AdjStep {
 };
 
 // One node of an adjoint step (interior or face node).
-// CG: the downstream adjoint field is written concurrently by other blocks.
-template <class L, class R, bool FACE, bool CG = false>
+template <class L, class R, bool FACE>
 __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<R>& P, int x, int y, int z, unsigned i,
                                              unsigned kf) {
   const Geo& g = A.geo;
@@ -972,12 +964,12 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) {
         const unsigned d = ft.dst[k * ft.n + kf], e = ft.ext[k * ft.n + kf];
-        a[k] = d != kNone ? ldf<CG>(bnext + (k * g.n + d)) : R(0);
-        if (e != kNone) a[k] += ldf<CG>(bnext + (k * g.n + e));
+        a[k] = d != kNone ? bnext[k * g.n + d] : R(0);
+        if (e != kNone) a[k] += bnext[k * g.n + e];
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < L::Q; ++k) a[k] = ldf<CG>(bnext + (k * g.n + i + offset<L>(g, k)));
+      for (int k = 0; k < L::Q; ++k) a[k] = bnext[k * g.n + i + offset<L>(g, k)];
     }
     raw_moments<L, R, true>(a, A0, A1, A2);
   }

@@ -9,8 +9,6 @@
 // native checkpoints), then runs K adjoint launches from the last state to
 // the first.  The design sensitivity of every adjoint step is added into a
 // per-node FP64 (sum, compensation) pair.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,14 +18,11 @@
 #include <cstring>
 #include <memory>
 #include <string>
-#include <unordered_map>
 #include <vector>
 
 #include "lbmadj.h"
 #include "filter.cuh"
-#include "flow.cuh"
 #include "kernels.cuh"
-#include "tma.cuh"
 
 namespace {
 
@@ -84,9 +79,8 @@ unsigned mask_with_cx(int sx) {
 struct Layout {
   size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gpart, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
       partials, acc, flags, f_idx, f_info, f_u0, f_src, f_dst, f_ext, xraw, xfilt, wfilt, slice_j, slice_c,
-      fl_band, fl_fband, fl_wptr, fl_widx, fl_done, total;
+      total;
   int nblocks_fwd, nblocks_1d, nslots;
-  int nblocks_sum;            // block-sum slots: per-step kernels' blocks or persistent bands
   int igx, igy, igz;          // interior grid (blocks of kBlock along x)
   size_t seg_sets;            // 2 when recompute and adjoint are pipelined
   unsigned nface;             // face nodes
@@ -182,14 +176,7 @@ Layout make_layout(const lbm_config& c) {
   L.gacc = take(n * 16);
   L.gpart = take(n * rs);
   L.gout = take(n * 8);
-  L.nblocks_sum = L.nblocks_fwd > lbm::kFlowMaxBands ? L.nblocks_fwd : lbm::kFlowMaxBands;
-  L.partials = take(size_t(L.nblocks_sum) * 32);
-  // persistent-step schedule: band bounds, face-row bounds, wait sets, progress
-  L.fl_band = take(size_t(lbm::kFlowMaxBands + 1) * 4);
-  L.fl_fband = take(size_t(lbm::kFlowMaxBands + 1) * 4);
-  L.fl_wptr = take(size_t(lbm::kFlowMaxBands + 1) * 4);
-  L.fl_widx = take(size_t(lbm::kFlowMaxBands) * lbm::kFlowMaxWait * 4);
-  L.fl_done = take(size_t(lbm::kFlowMaxBands) * 4);
+  L.partials = take(size_t(L.nblocks_fwd) * 32);
   L.f_idx = take(size_t(L.nface) * 4);
   L.f_info = take(size_t(L.nface) * 4);
   L.f_u0 = take(size_t(L.nface) * 4);
@@ -235,13 +222,6 @@ struct Impl {
   virtual void to_double(const void* src) = 0;
   virtual void encode(const void* p, int slot) = 0;
   virtual void decode(int slot, void* p) = 0;
-  // Persistent step kernels (see flow.cuh).
-  virtual int flow_capacity() = 0;   // co-resident blocks of the persistent kernels, 0 if none
-  virtual void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every,
-                       void* mom = nullptr) = 0;
-  virtual void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
-                       int nsteps, int step0) = 0;
-  virtual bool tma_setup() = 0;      // encoder and launch shape of the TMA-staged kernels
   // Field of checkpoint s of the last window (decoded if need be), in this context's precision.
   virtual const void* checkpoint_field(int s) = 0;
   // dst (this context's precision) <- src field in precision rs_src.
@@ -271,12 +251,6 @@ struct lbm_ctx {
   cudaEvent_t fork_cur = nullptr, join_cur = nullptr;
   bool use_graphs = true;
   bool use_pdl = true;        // programmatic dependent launch of the step kernels
-  bool tma_ok = false;        // TMA-staged interior kernels available (row pitch a multiple of 16 bytes)
-  bool use_tma = false;       // forward interior steps through fwd_tma_kernel
-  int flow_bands = 0;         // bands of the persistent schedule (0: not available)
-  bool use_flow = false;      // run segments as persistent launches
-  unsigned long long flow_wait_ns = 4000000000ull;   // 4 s without progress of a neighbouring band
-  int flow_silent = -1;       // test hook: a band that never publishes
   int64_t kernels = 0;        // kernel launches enqueued so far
   int64_t kernels_window = 0, kernels_adjoint = 0;   // per window / per adjoint sweep, as last enqueued
   lbm_ctx* along = nullptr;   // lbm_step_window_along: the context whose checkpoints start each segment
@@ -504,15 +478,10 @@ struct ImplT final : Impl {
   void fwd(const void* src, void* dst, int sample, void* mom) override {
     const lbm::FwdArgs<R> A = fwd_args(src, dst, sample, mom);
     const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
-    const CUtensorMap* map = c->use_tma ? tensor_map(src) : nullptr;
     // the step that writes a moment checkpoint runs its own instantiation (MOM)
     fork_join(
         [&](cudaStream_t st) {
-          int* status = c->template at<int>(c->lay.flags) + 2;
-          const unsigned gx = unsigned(c->lay.igx), gy = unsigned(c->lay.igy);
-          if (map && mom) launch_tma(lbm::fwd_tma_kernel<L, R, true>, st, *map, A, blk0, gx, gy, status);
-          else if (map) launch_tma(lbm::fwd_tma_kernel<L, R, false>, st, *map, A, blk0, gx, gy, status);
-          else if (mom) launch(lbm::fwd_interior_kernel<L, R, true>, igrid(), st, A);
+          if (mom) launch(lbm::fwd_interior_kernel<L, R, true>, igrid(), st, A);
           else launch(lbm::fwd_interior_kernel<L, R, false>, igrid(), st, A);
         },
         [&](cudaStream_t st) {
@@ -541,68 +510,6 @@ struct ImplT final : Impl {
         });
   }
 
-  // TMA-staged interior kernels (tma.cuh).
-  PFN_cuTensorMapEncodeTiled_v12000 encode_map = nullptr;
-  std::unordered_map<const void*, CUtensorMap> maps;
-  int tma_grid = 0;
-  bool tma_setup() override {
-    const lbm_config& k = c->cfg;
-    if (!has_interior() || (size_t(k.nx) * sizeof(R)) % 16 != 0) return false;
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-      cudaGetLastError();
-      return false;
-    }
-    encode_map = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    const size_t smem = lbm::fwd_tma_smem<L, R>();
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaFuncSetAttribute(lbm::fwd_tma_kernel<L, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
-        cudaFuncSetAttribute(lbm::fwd_tma_kernel<L, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::fwd_tma_kernel<L, R, true>, lbm::kBlock, smem) != cudaSuccess ||
-        per_sm < 1) {
-      cudaGetLastError();
-      return false;
-    }
-    const long long tiles = (long long)c->lay.igx * c->lay.igy * c->lay.igz;
-    tma_grid = int(std::min<long long>(tiles, (long long)sms * per_sm));
-    return tensor_map(c->lattice(0)) != nullptr;
-  }
-  // The tensor map of a population field at base: {nx, ny, nz Q}, one box of
-  // kTmaBox x 1 x 1 elements.  Encoded once per field address.
-  const CUtensorMap* tensor_map(const void* base) {
-    auto it = maps.find(base);
-    if (it != maps.end()) return &it->second;
-    const lbm_config& k = c->cfg;
-    CUtensorMap m;
-    const cuuint64_t dims[3] = {cuuint64_t(k.nx), cuuint64_t(k.ny), cuuint64_t(k.nz) * L::Q};
-    const cuuint64_t strides[2] = {cuuint64_t(k.nx) * sizeof(R), cuuint64_t(k.nx) * k.ny * sizeof(R)};
-    const cuuint32_t box[3] = {cuuint32_t(lbm::kTmaBox), 1, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = encode_map(&m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                                  3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return nullptr;
-    return &maps.emplace(base, m).first->second;
-  }
-  template <class... Args>
-  void launch_tma(void (*kernel)(const CUtensorMap, Args...), cudaStream_t st, const CUtensorMap& map, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(tma_grid);
-    cfg.blockDim = dim3(lbm::kBlock);
-    cfg.dynamicSmemBytes = lbm::fwd_tma_smem<L, R>();
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = c->use_pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kernel, map, args...);
-  }
   void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
     const lbm::AdjArgs<R> A = adj_args(bnext, pprev, bout, sample);
     fork_join([&](cudaStream_t st) { launch(lbm::adj_interior_kernel<L, R>, igrid(), st, A); },
@@ -626,63 +533,6 @@ struct ImplT final : Impl {
                                                                         static_cast<R*>(dst), total);
   }
 
-  // Persistent step kernels.
-  int flow_capacity() override {
-    int dev = 0, sms = 0, coop = 0, bf = 0, ba = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, lbm::fwd_flow_kernel<L, R>, lbm::kFlowBlock, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, lbm::adj_flow_kernel<L, R>, lbm::kFlowBlock, 0) != cudaSuccess) {
-      cudaGetLastError();
-      return 0;
-    }
-    if (!coop) return 0;
-    return sms * (bf < ba ? bf : ba);
-  }
-  lbm::Flow flow() const {
-    lbm::Flow f;
-    f.band = c->template at<unsigned>(c->lay.fl_band);
-    f.fband = c->template at<unsigned>(c->lay.fl_fband);
-    f.wptr = c->template at<int>(c->lay.fl_wptr);
-    f.widx = c->template at<int>(c->lay.fl_widx);
-    f.done = c->template at<int>(c->lay.fl_done);
-    f.status = c->template at<int>(c->lay.flags) + 2;
-    f.blk = c->template at<double>(c->lay.partials);
-    f.wait_ns = c->flow_wait_ns;
-    f.silent = c->flow_silent;
-    return f;
-  }
-  // Cooperative launch of P bands (all blocks co-resident) after clearing
-  // the progress counters.
-  template <class... Args>
-  void launch_flow(void (*kernel)(Args...), Args... args) {
-    cudaMemsetAsync(c->template at<int>(c->lay.fl_done), 0, size_t(c->flow_bands) * 4, c->ls);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(c->flow_bands);
-    cfg.blockDim = dim3(lbm::kFlowBlock);
-    cfg.stream = c->ls;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, args...);
-    c->kernels += 1;
-  }
-  void fwd_run(void* a, void* b, size_t stride_bytes, int nsteps, int step0, int sample_every, void* mom) override {
-    const lbm::FwdArgs<R> A = fwd_args(nullptr, nullptr, 0, mom);
-    const lbm::Chain<R> ch{static_cast<R*>(a), static_cast<R*>(b), (long long)(stride_bytes / sizeof(R))};
-    launch_flow(lbm::fwd_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, sample_every, c->sample_from);
-  }
-  void adj_run(const void* p0, const void* p1, size_t stride_bytes, const void* bnext0, void* o0, void* o1,
-               int nsteps, int step0) override {
-    const lbm::AdjArgs<R> A = adj_args(nullptr, nullptr, nullptr, 0);
-    const lbm::AdjChain<R> ch{static_cast<const R*>(p0), static_cast<const R*>(p1),
-                              (long long)(stride_bytes / sizeof(R)), static_cast<const R*>(bnext0),
-                              static_cast<R*>(o0), static_cast<R*>(o1)};
-    launch_flow(lbm::adj_flow_kernel<L, R>, A, ch, flow(), nsteps, step0, c->cfg.sample_every, c->sample_from);
-  }
   void pull(const void* b, void* out) override {
     lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(
         static_cast<const R*>(b), c->template at<uint8_t>(c->lay.cls), static_cast<R*>(out), c->geo);
@@ -840,16 +690,11 @@ lbm_status enqueue_window(lbm_ctx* c) {
     // moment checkpoints: the segment's last step also stores checkpoint s + 1
     void* mom = moment && s + 1 < S ? c->ckpt_mom(s + 1) : nullptr;
     e = c->begin();
-    if (c->use_flow) {   // the K steps of the segment in one persistent launch
-      c->impl->fwd_run(c->lattice(c->cur), c->lattice(c->cur ^ 1), 0, K, s * K, k.sample_every, mom);
-      c->cur ^= K & 1;
-    } else {
-      for (int j = 0; j < K; ++j) {
-        const int step = s * K + j;
-        c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), lbm::sampled_step(step, c->sample_from, k.sample_every),
-                     j == K - 1 ? mom : nullptr);
-        c->cur ^= 1;
-      }
+    for (int j = 0; j < K; ++j) {
+      const int step = s * K + j;
+      c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), lbm::sampled_step(step, c->sample_from, k.sample_every),
+                   j == K - 1 ? mom : nullptr);
+      c->cur ^= 1;
     }
     c->end(e, 0, K, int64_t(K) * int64_t(c->n));
   }
@@ -857,15 +702,14 @@ lbm_status enqueue_window(lbm_ctx* c) {
       k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
   const double nsamples = double((k.window_len - c->sample_from) / k.sample_every);
   if (k.lattice == LBM_D2Q9) {
-    // persistent bands (single lattice only) sum as one flat run of block sums
     lbm::slice_end_kernel<<<k.nz, lbm::kEndThreads, 0, c->ls>>>(
         c->at<double>(c->lay.partials), c->lay.igx, c->lay.igy, c->lay.fbs, c->lay.igx * c->lay.igy * c->lay.igz,
         nsamples, c->at<double>(c->lay.slice_c), mon_scale, k.monitor_kind,
-        c->at<double>(c->lay.slice_j), c->use_flow ? c->lay.nblocks_sum : 0);
+        c->at<double>(c->lay.slice_j));
     c->kernels += 1;
   }
   lbm::window_end_kernel<<<1, lbm::kEndThreads, 0, c->ls>>>(
-      c->at<double>(c->lay.partials), c->lay.nblocks_sum, c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol,
+      c->at<double>(c->lay.partials), c->lay.nblocks_fwd, c->at<lbm::WindowAcc>(c->lay.acc), k.conv_tol,
       c->at<int>(c->lay.flags), nsamples, c->jconst, mon_scale, k.monitor_kind);
   c->kernels += 1;
   c->kernels_window = c->kernels - k0;
@@ -882,8 +726,7 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
   const lbm_config& k = c->cfg;
   const int K = k.ckpt_every, S = c->lay.nslots;
   const bool native = k.ckpt_format == LBM_CKPT_NATIVE;
-  const bool flow = c->use_flow;
-  const bool pipe = c->lay.seg_sets == 2 && !flow;   // persistent launches own the whole GPU: serial
+  const bool pipe = c->lay.seg_sets == 2;
   const size_t lat = align_up(c->q * c->n * c->rs);
   const int64_t k0 = c->kernels;
   CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gacc), 0, c->n * 16, c->ls));
@@ -902,11 +745,7 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
     if (restore) c->impl->decode(s, c->seg_slot(s, 0));
     c->end(e, 3, restore ? 1 : 0, 0);
     e = c->begin();
-    if (flow) {
-      if (K > 1) c->impl->fwd_run(c->seg_slot(s, 0), c->seg_slot(s, 1), lat, K - 1, 0, 0);
-    } else {
-      for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
-    }
+    for (int j = 1; j < K; ++j) c->impl->fwd(c->seg_slot(s, j - 1), c->seg_slot(s, j), 0);
     c->end(e, 1, K - 1, int64_t(K - 1) * int64_t(c->n));
   };
   if (pipe) {
@@ -933,121 +772,17 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
       cudaStreamWaitEvent(main, c->rec_done[s & 1], 0);
     }
     cudaEvent_t e = c->begin();
-    if (flow) {   // step s K + j for j = K-1 .. 0 in one persistent launch
-      c->impl->adj_run(c->seg_slot(s, 0), K > 1 ? c->seg_slot(s, 1) : nullptr, lat, bnext, c->adjbuf(bo),
-                       c->adjbuf(bo ^ 1), K, s * K);
-      bnext = c->adjbuf(bo ^ ((K - 1) & 1));
-      bo ^= K & 1;
-    } else {
-      for (int j = K - 1; j >= 0; --j) {
-        const int step = s * K + j;
-        c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), lbm::sampled_step(step, c->sample_from, k.sample_every));
-        bnext = c->adjbuf(bo);
-        bo ^= 1;
-      }
+    for (int j = K - 1; j >= 0; --j) {
+      const int step = s * K + j;
+      c->impl->adj(bnext, c->seg_slot(s, j), c->adjbuf(bo), lbm::sampled_step(step, c->sample_from, k.sample_every));
+      bnext = c->adjbuf(bo);
+      bo ^= 1;
     }
     c->end(e, 2, K, int64_t(K) * int64_t(c->n));
     c->impl->fold();
     if (pipe) cudaEventRecord(c->adj_done[s & 1], main);
   }
   c->kernels_adjoint = c->kernels - k0;
-  return LBM_OK;
-}
-
-// Schedule of the persistent step kernels (flow.cuh): P bands of consecutive
-// node indices, cut where the running cost crosses b/P of the total (a face
-// node costs kFaceCost interior nodes: a table gather and boundary rule), the
-// face-table rows of each band, and each band's wait set W(b) = deps(b) u
-// rdeps(b) \ {b}, where deps(b) holds every band that a node of b pulls from
-// (forward) or pushes to (adjoint).  Interior nodes never wrap, so their reads
-// lie within the largest lattice offset of the band; face nodes list theirs
-// in the table.  P starts at the number of co-resident blocks and halves
-// until every wait set fits.  The schedule is for a single lattice: D2Q9
-// batches keep the per-step kernels.
-template <class L>
-lbm_status build_flow(lbm_ctx* c, const std::vector<unsigned>& idx, const std::vector<unsigned>& src,
-                      const std::vector<unsigned>& dst, const std::vector<unsigned>& ext) {
-  const lbm_config& k = c->cfg;
-  c->flow_bands = 0;
-  if (L::D == 2 && k.nz != 1) return LBM_OK;
-  int P = c->impl->flow_capacity();
-  const size_t n = c->n;
-  const size_t per_block = lbm::kFlowBlock;
-  if (size_t(P) > (n + per_block - 1) / per_block) P = int((n + per_block - 1) / per_block);
-  if (P > lbm::kFlowMaxBands) P = lbm::kFlowMaxBands;
-  if (P < 1) return LBM_OK;
-  const unsigned nf = c->lay.nface;
-  size_t nreal = 0;   // face rows with a node (padding, if any, sits at the end)
-  while (nreal < idx.size() && idx[nreal] != lbm::kNone) ++nreal;
-  const bool d3 = L::D == 3;
-  auto is_face = [&](size_t i) {
-    const size_t x = i % k.nx, y = (i / k.nx) % k.ny, z = i / (size_t(k.nx) * k.ny);
-    return x == 0 || x == size_t(k.nx) - 1 || y == 0 || y == size_t(k.ny) - 1 ||
-           (d3 && (z == 0 || z == size_t(k.nz) - 1));
-  };
-  constexpr double kFaceCost = 3.0;
-  const double total = double(n) + (kFaceCost - 1.0) * double(nreal);
-  const size_t reach = d3 ? size_t(k.nx) * k.ny + k.nx + 1 : size_t(k.nx) + 1;
-  for (; P >= 1; P /= 2) {
-    std::vector<unsigned> band(size_t(P) + 1), fband(size_t(P) + 1);
-    band[0] = 0;
-    {
-      double run = 0.0;
-      int b = 1;
-      for (size_t i = 0; i < n && b < P; ++i) {
-        while (b < P && run >= total * double(b) / double(P)) band[size_t(b++)] = unsigned(i);
-        run += is_face(i) ? kFaceCost : 1.0;
-      }
-      while (b < P) band[size_t(b++)] = unsigned(n);
-      band[size_t(P)] = unsigned(n);
-    }
-    for (int b = 0; b <= P; ++b)
-      fband[size_t(b)] = unsigned(std::lower_bound(idx.begin(), idx.begin() + nreal, band[size_t(b)]) - idx.begin());
-    auto band_of = [&](unsigned i) {
-      return int(std::upper_bound(band.begin(), band.end(), i) - band.begin()) - 1;
-    };
-    std::vector<std::vector<int>> deps(static_cast<size_t>(P));
-    for (int b = 0; b < P; ++b) {
-      std::vector<int>& d = deps[size_t(b)];
-      const unsigned lo = band[size_t(b)], hi = band[size_t(b) + 1];
-      if (lo == hi) continue;
-      const unsigned rlo = lo > reach ? unsigned(lo - reach) : 0u;
-      const unsigned rhi = size_t(hi) + reach < n ? unsigned(hi + reach) : unsigned(n);
-      for (int t = band_of(rlo); t < P && band[size_t(t)] < rhi; ++t) d.push_back(t);
-      for (unsigned r = fband[size_t(b)]; r < fband[size_t(b) + 1]; ++r)
-        for (int a = 0; a < L::Q; ++a)
-          for (unsigned j : {src[size_t(a) * nf + r], dst[size_t(a) * nf + r], ext[size_t(a) * nf + r]})
-            if (j != lbm::kNone) d.push_back(band_of(j));
-    }
-    std::vector<std::vector<int>> wait(static_cast<size_t>(P));
-    for (int b = 0; b < P; ++b)
-      for (int t : deps[size_t(b)])
-        if (t != b) {
-          wait[size_t(b)].push_back(t);
-          wait[size_t(t)].push_back(b);
-        }
-    bool fits = true;
-    std::vector<int> wptr(size_t(P) + 1, 0), widx;
-    for (int b = 0; b < P && fits; ++b) {
-      std::vector<int>& w = wait[size_t(b)];
-      std::sort(w.begin(), w.end());
-      w.erase(std::unique(w.begin(), w.end()), w.end());
-      if (w.size() > size_t(lbm::kFlowMaxWait)) fits = false;
-      widx.insert(widx.end(), w.begin(), w.end());
-      wptr[size_t(b) + 1] = int(widx.size());
-    }
-    if (!fits) continue;
-    cudaStream_t s = c->stream;
-    const Layout& lay = c->lay;
-    CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_band), band.data(), band.size() * 4, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_fband), fband.data(), fband.size() * 4, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_wptr), wptr.data(), wptr.size() * 4, cudaMemcpyHostToDevice, s));
-    if (!widx.empty())
-      CUDA_TRY(cudaMemcpyAsync(c->at(lay.fl_widx), widx.data(), widx.size() * 4, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    c->flow_bands = P;
-    return LBM_OK;
-  }
   return LBM_OK;
 }
 
@@ -1129,7 +864,6 @@ lbm_status build_face_table(lbm_ctx* c, const uint8_t* cls, const float* inlet_u
   }
   if (!d3) pad_to(nf);
   if (idx.size() != nf) return fail(LBM_ERR_ARG, "face count mismatch");
-  LBM_TRY(build_flow<L>(c, idx, src, dst, ext));
   cudaStream_t s = c->stream;
   CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_idx), idx.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_info), info.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
@@ -1250,7 +984,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   const size_t n = ctx->n;
   cudaStream_t s = ctx->stream;
   CUDA_TRY(cudaMemsetAsync(x->at(lay.f[0]), 0, align_up(ctx->q * n * ctx->rs), s));   // rest equilibrium
-  CUDA_TRY(cudaMemsetAsync(x->at(lay.partials), 0, size_t(lay.nblocks_sum) * 32, s));
+  CUDA_TRY(cudaMemsetAsync(x->at(lay.partials), 0, size_t(lay.nblocks_fwd) * 32, s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.acc), 0, sizeof(lbm::WindowAcc), s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.flags), 0, 16, s));
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.cls), node_class, n, cudaMemcpyDefault, s));
@@ -1315,7 +1049,6 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   x->impl->set_design();
   CUDA_TRY(cudaGetLastError());
   LBM_TRY(check_flags(x, 1, LBM_ERR_ARG, "design values must lie in [0, 1]"));
-  x->tma_ok = x->impl->tma_setup();
   *out = ctx.release();
   return LBM_OK;
 }
@@ -1341,12 +1074,6 @@ lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window)
   if (c->use_graphs) c->harvest_graph(c->gwin[cur0][c->timing ? 1 : 0]);
   c->harvest();
   c->steps += k.window_len;
-  if (acc.stalled) {
-    CUDA_TRY(cudaMemsetAsync(c->at<int>(c->lay.flags) + 2, 0, sizeof(int), c->stream));
-    c->window_valid = false;
-    c->grad_valid = false;
-    return fail(LBM_ERR_CUDA, "a step kernel timed out waiting (for a neighbouring band or a TMA copy)");
-  }
   if (acc.nonfinite) {
     c->window_valid = false;
     c->grad_valid = false;
@@ -1388,11 +1115,10 @@ lbm_status lbm_step_window_along(lbm_ctx* c, lbm_ctx* ref, double* J_window, dou
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->harvest();
   c->steps += k.window_len;
-  if (acc.stalled || acc.nonfinite) {
-    CUDA_TRY(cudaMemsetAsync(c->at<int>(c->lay.flags) + 2, 0, sizeof(int), c->stream));
+  if (acc.nonfinite) {
     c->window_valid = false;
     c->grad_valid = false;
-    return fail(acc.stalled ? LBM_ERR_CUDA : LBM_ERR_NONFINITE, "the window along the reference failed");
+    return fail(LBM_ERR_NONFINITE, "the window along the reference produced a non-positive density or a non-finite value");
   }
   c->windows += 1;
   c->window_valid = true;
@@ -1444,10 +1170,6 @@ lbm_status lbm_adjoint_window(lbm_ctx* c, double* J_eff) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (G) c->harvest_graph(*G);
   c->harvest();
-  if (c->use_flow || c->use_tma) {
-    c->grad_valid = false;
-    LBM_TRY(check_flags(c, 2, LBM_ERR_CUDA, "a step kernel timed out waiting (for a neighbouring band or a TMA copy)"));
-  }
   // The sweep runs an even or odd number of adjoint steps: b^{n0} is in buffer (W-1) & 1.
   c->bout_last = (c->cfg.window_len - 1) & 1;
   c->grad_valid = true;
@@ -1659,31 +1381,6 @@ lbm_status lbm_set_pdl(lbm_ctx* c, int32_t enable) {
   return LBM_OK;
 }
 
-lbm_status lbm_set_flow(lbm_ctx* c, int32_t enable) {
-  if (!c) return fail(LBM_ERR_ARG, "null context");
-  if (enable && c->flow_bands == 0)
-    return fail(LBM_ERR_ARG, "persistent step kernels are unavailable here (D2Q9 batches, or no cooperative launch)");
-  if ((enable != 0) != c->use_flow) {
-    // captured graphs hold the other launch sequence: capture again on next use
-    for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);
-    for (auto& g : c->gadj) c->drop_graph(g);
-  }
-  c->use_flow = enable != 0;
-  return LBM_OK;
-}
-
-lbm_status lbm_set_tma(lbm_ctx* c, int32_t enable) {
-  if (!c) return fail(LBM_ERR_ARG, "null context");
-  if (enable && !c->tma_ok)
-    return fail(LBM_ERR_ARG, "TMA staging needs an interior and nx * element size a multiple of 16 bytes");
-  if ((enable != 0) != c->use_tma) {
-    for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);
-    for (auto& g : c->gadj) c->drop_graph(g);
-  }
-  c->use_tma = enable != 0;
-  return LBM_OK;
-}
-
 lbm_status lbm_set_sample_start(lbm_ctx* c, int32_t first) {
   if (!c) return fail(LBM_ERR_ARG, "null context");
   const lbm_config& k = c->cfg;
@@ -1700,25 +1397,10 @@ lbm_status lbm_set_sample_start(lbm_ctx* c, int32_t first) {
   return LBM_OK;
 }
 
-lbm_status lbm_set_flow_test_hook(lbm_ctx* c, double wait_seconds, int32_t silent_band) {
-  if (!c) return fail(LBM_ERR_ARG, "null context");
-  if (!(wait_seconds > 0.0 && wait_seconds <= 60.0)) return fail(LBM_ERR_ARG, "wait_seconds must be in (0, 60]");
-  if (silent_band < -1 || silent_band >= c->flow_bands) return fail(LBM_ERR_ARG, "silent_band out of range");
-  for (auto& row : c->gwin) for (auto& g : row) c->drop_graph(g);   // graphs hold the old parameters
-  for (auto& g : c->gadj) c->drop_graph(g);
-  c->flow_wait_ns = static_cast<unsigned long long>(wait_seconds * 1e9);
-  c->flow_silent = silent_band;
-  return LBM_OK;
-}
-
 lbm_status lbm_get_schedule(lbm_ctx* c, lbm_schedule* out) {
   if (!c || !out) return fail(LBM_ERR_ARG, "null argument");
-  out->flow_bands = c->flow_bands;
-  out->flow = c->use_flow ? 1 : 0;
   out->graphs = c->use_graphs ? 1 : 0;
   out->pdl = c->use_pdl ? 1 : 0;
-  out->tma_available = c->tma_ok ? 1 : 0;
-  out->tma = c->use_tma ? 1 : 0;
   out->kernels_window = c->kernels_window;
   out->kernels_adjoint = c->kernels_adjoint;
   return LBM_OK;

@@ -308,13 +308,19 @@ lbm_status lbm_get_schedule(lbm_ctx* ctx, lbm_schedule* out);
 lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);
 
 /* One forward window, like lbm_step_window, for callers that cannot allocate
- * device memory (code running while a CUDA graph is being captured, hosts
- * that hand out only pre-registered buffers, sandboxes without access to the
- * allocator).  There is no counterpart in the paper: it is a deployment aid.
+ * device memory: a host process that hands this library only buffers it
+ * registered up front (a serving runtime with a fixed memory pool, a plug-in
+ * living inside another application's allocator), or a sandbox that does not
+ * expose the CUDA allocator.  There is no counterpart in the paper: it is a
+ * deployment aid.
  *   cfg                 as for lbm_create (precision must be LBM_FP32; the
  *                       checkpoint fields are ignored)
- *   node_class          device, uint8 [N], obeying the rules of lbm_create
- *                       (not re-checked here)
+ *   node_class          device, uint8 [N]: a map that lbm_create would accept.
+ *                       It is not checked on the host; every node checks its
+ *                       own class on the device, and a map that breaks the
+ *                       rules (class out of range, a non-FLUID interior node,
+ *                       a boundary class on the wrong face) fails the call
+ *                       with LBM_ERR_ARG, leaving pop undefined
  *   design_gamma, objective_weights
  *                       device, float [N]
  *   inlet_u             device, float [nz][ny]
@@ -325,14 +331,20 @@ lbm_status lbm_get_counters(lbm_ctx* ctx, int64_t* steps, int64_t* windows);
  *   pop_tmp             device, float [Q][N], caller-owned second buffer
  *   stream              cudaStream_t to enqueue on (NULL = legacy default)
  * Returns the window means of the objective and the monitor like
- * lbm_step_window, and synchronises the stream.  It allocates nothing: its
- * only scratch is a 512 KiB + 256 B array inside the library image, present
- * on every GPU that loads the library until the process exits.  Limit: at most
- * 16384 blocks of 128 nodes, i.e. ceil(nx/128) * ny * nz <= 16384; larger
- * lattices return LBM_ERR_ARG.  The first call on a device looks up the
- * array's device address (make that first call before any stream capture).
- * All calls share the array: calls that overlap on the GPU race.  No
- * checkpoints are stored, so lbm_adjoint_window cannot follow it. */
+ * lbm_step_window.  The call reads them back to the host and waits for the
+ * stream before it returns; a stream that is capturing a CUDA graph is
+ * refused with LBM_ERR_ARG before anything is enqueued.  It allocates
+ * nothing: its only scratch is a 512 KiB + 256 B array inside the library
+ * image, present on every GPU that loads the library until the process exits.
+ * Limit: at most 16384 blocks of 128 nodes, i.e. ceil(nx/128) * ny * nz <=
+ * 16384; larger lattices return LBM_ERR_ARG.  The first call on a device
+ * looks up the array's device address.  All calls share the array and each
+ * call clears what it needs at zero: calls that overlap on the GPU race.  g(phi) is
+ * evaluated per node and step from gamma in FP64 (the rounding of the design
+ * kernel), and the pressure objective samples cs^2 rho directly, so the
+ * window means agree with lbm_step_window's to FP32 summation error.  No
+ * checkpoints are stored, so lbm_adjoint_window cannot follow it.  Every
+ * failure sets lbm_last_error. */
 lbm_status lbm_step_window_noalloc(const lbm_config* cfg, const uint8_t* node_class, const float* design_gamma,
                                    const float* objective_weights, const float* inlet_u, float* pop,
                                    float* pop_tmp, void* stream, double* J_window, double* monitor_window);

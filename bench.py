@@ -1,19 +1,22 @@
 """Benchmark: forward window + discrete adjoint of the windowed LBM-LES.
 
-One step = one pass of the whole hot path on the cylinder-wake workload
-(D2Q9 1024x256, Re 200, |W| = 2000, checkpoints every 100 steps, FP32):
-a forward window of 2000 fused collide-stream launches with sampling and
-checkpoints, the window-end reduction and the consecutive-window test, the
-discrete adjoint over that window (20 segments recomputed from their
-checkpoints, 2000 adjoint launches) and the design gradient.
+One step = one pass of the whole hot path on the largest single-GPU workload,
+the D3Q19 U-bend duct 384x192x192 (14.2 M nodes, Re 3000, Cs 0.15,
+|W| = 2000, FP32 populations, BF16 checkpoints every 50 steps): a forward
+window of 2000 fused collide-stream steps with sampling and checkpoints, the
+window-end reduction and the consecutive-window test, the discrete adjoint
+over that window (40 segments recomputed from their checkpoints, 2000 adjoint
+steps) and the design gradient.
 
 value = (forward + adjoint) lattice updates / second over all ranks, in MLUPS.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-``--impl reference`` times the FP64 CPU oracle instead (on this host's cores,
-on a bounded sample of the same workload).  Under torchrun each rank runs an
-independent replica (the path is one GPU per problem).
+``--impl reference`` times the FP64 CPU oracle instead, on this host's cores,
+on a bounded sample of the same workload (for the U-bends, the same duct
+scaled down so that the oracle's per-node Jacobians fit in host memory).
+Under torchrun each rank runs an independent replica (the path is one GPU per
+problem).
 """
 from __future__ import annotations
 
@@ -29,13 +32,14 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# The CPU oracle is timed on one thread: pin every BLAS / OpenMP pool to one
-# thread before numpy loads, so that the reported core count is exact.
+# Each CPU oracle process runs on one thread: pin every BLAS / OpenMP pool to
+# one thread before numpy loads (spawned workers inherit it), so that the
+# reported core count is exact.
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 METRIC = "forward & adjoint MLUPS and % HBM roofline, FP32/mixed vs FP64 at stated error"
-WORKLOAD = "wake1024x256"
+WORKLOAD = "ubend384x192x192"
 CKPT_NAMES = ["fp32", "fp16", "bf16", "moment"]   # lbm_config.ckpt_format
 KERNEL_SRC = os.path.join(ROOT, "paper_2608_19617_b300", "csrc", "kernels.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
@@ -74,6 +78,10 @@ def parse():
                     help="the sensitivity validation of Sec. 4.2.1 on the cylinder case: finite differences "
                          "(perturbations 1e-3 and 1e-4, FP64 batches of independent slices) against the adjoint "
                          "at 60 points in the downstream half of the cylinder")
+    ap.add_argument("--ckpt-sweep", action="store_true",
+                    help="checkpoint-storage sweep: FP32, FP16 and BF16 checkpoints of the FP32 adjoint against "
+                         "the FP64 GPU adjoint along the same trajectory (gradient cosine, J error, sweep time, "
+                         "workspace)")
     ap.add_argument("--full-time-k", type=int, default=1,
                     help="checkpoint interval of the full-time run (1: the complete history)")
     ap.add_argument("--full-time-cap-gb", type=float, default=96.0,
@@ -168,6 +176,23 @@ def bytes_per_lu(case, phase, rs=4):
     return (3 * q + 1) * rs + 2.0 * rs * nd / n + 4.0 * no / n / case.sample_every
 
 
+def survey_bytes_per_lu(case, unit, rs=4):
+    """The scope table's algorithmic bytes per lattice update of a unit of
+    work: forward (2Q + 1) 4 B (D2Q9 76, D3Q19 156; FP64 148 / 308); adjoint
+    sweep step = adjoint kernel (12Q + 4 + 32 B: two population reads, one
+    write, g, an FP64 (sum, comp) accumulator read and written per step) plus
+    a recompute step and a segment store (D2Q9 256, D3Q19 496), twice that in
+    FP64.  This count is an upper bound for this design, which folds an FP32
+    per-segment partial (8 B per design node per step, not 32) and whose
+    recompute writes each state once (no separate store); bytes_per_lu() is
+    the design's own count."""
+    q = case.lattice
+    fwd = {9: 76, 19: 156}[q] if rs == 4 else {9: 148, 19: 308}[q]
+    if unit == "forward step":
+        return fwd
+    return {9: 256, 19: 496}[q] * (rs // 4)
+
+
 def kernel_hash():
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
@@ -246,29 +271,107 @@ def peaks():
 
 # ------------------------------------------------------------ CPU oracle --
 
-def oracle_sample(case, fwd_steps, seconds_hint=None):
-    """Time the FP64 oracle on a bounded sample of the workload: a window of
-    ``fwd_steps`` steps from a developed-looking start, then its adjoint."""
-    import contextlib
+# Largest lattice the oracle times in one process: its adjoint assembles the
+# literal Q x Q Jacobian of every node (Q^2 N doubles, plus temporaries).
+ORACLE_MAX_JAC_BYTES = 0.1e9
 
+
+def oracle_case(case):
+    """The bounded sample of a workload that the oracle is timed on: the
+    workload itself when its per-node Jacobians fit in ORACLE_MAX_JAC_BYTES,
+    otherwise (the 3D U-bends) the same duct scaled down by the smallest
+    integer factor that fits, with the same tau, Cs, inlet speed and objective."""
+    from paper_2608_19617_b300 import inputs as I
+    if case.lattice ** 2 * case.n * 8 <= ORACLE_MAX_JAC_BYTES:
+        return case, 1
+    if not case.name.startswith("ubend"):
+        raise SystemExit(f"no bounded oracle sample for {case.name}")
+    lf = int(case.monitor_l)
+    for f in range(2, lf + 1):
+        if lf % f or case.nx % f or case.ny % f or case.nz % f:
+            continue
+        c = I.ubend_case(case.nx // f, case.ny // f, case.nz // f, lf // f, tau=case.tau, cs_smag=case.cs_smag,
+                         window_len=case.window_len, ckpt_every=case.ckpt_every, ckpt_format=case.ckpt_format,
+                         name=f"{case.name}/{f}")
+        if case.lattice ** 2 * c.n * 8 <= ORACLE_MAX_JAC_BYTES:
+            return c, f
+    raise SystemExit(f"no bounded oracle sample for {case.name}")
+
+
+def oracle_sample(case, fwd_steps):
+    """Time the FP64 oracle, as it stands, on one thread: a window of
+    ``fwd_steps`` steps from rest, then its adjoint.  Returns MLUPS over both."""
     from oracle import lbm as O
-    try:
-        from threadpoolctl import threadpool_limits
-        limit = threadpool_limits(limits=1)
-    except ImportError:
-        limit = contextlib.nullcontext()
-    c = case.replace(window_len=fwd_steps, ckpt_every=fwd_steps, sample_every=1)
-    with limit:
-        pr = O.Problem(c)
-        p0 = pr.initial_state()
-        t0 = time.perf_counter()
-        _, J, M, traj = pr.run_window(p0)
-        t1 = time.perf_counter()
-        pr.adjoint_window(traj)
-        t2 = time.perf_counter()
+    c = case.replace(window_len=fwd_steps, ckpt_every=fwd_steps, sample_every=1, sample_from=0)
+    pr = O.Problem(c)
+    p0 = pr.initial_state()
+    t0 = time.perf_counter()
+    _, J, M, traj = pr.run_window(p0)
+    t1 = time.perf_counter()
+    pr.adjoint_window(traj)
+    t2 = time.perf_counter()
     lus = 2 * fwd_steps * c.n
     return {"value": lus / (t2 - t0) / 1e6, "fwd_s": t1 - t0, "adj_s": t2 - t1, "seconds": t2 - t0,
-            "lattice_updates": lus, "cores": 1}
+            "lattice_updates": lus}
+
+
+def _oracle_worker(args):
+    """One spawned process: build the sample case and time it (args = workload
+    name, step count, repeats)."""
+    name, fwd_steps, reps = args
+    from paper_2608_19617_b300 import inputs as I
+    c, _ = oracle_case(I.WORKLOADS[name]())
+    return [oracle_sample(c, fwd_steps) for _ in range(reps)]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_processes(case_sample):
+    """Processes for the all-core oracle timing: one per host core, fewer if
+    the host's available memory would not hold that many oracle working sets
+    (about 40 Q^2 N bytes each, the Jacobian and its temporaries, plus 0.3 GB)."""
+    per = 40 * case_sample.lattice ** 2 * case_sample.n + 0.3e9
+    avail = None
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                avail = float(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    n = host_cores()
+    if avail:
+        n = max(1, min(n, int(0.5 * avail // per)))
+    return n
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: P spawned single-thread processes,
+    each timing its own replica of the sample (the oracle is a serial numpy
+    program; replicas are how it uses a many-core host).  Throughput = all
+    processes' lattice updates over the wall time of the batch."""
+
+    def __init__(self, workload, procs):
+        import multiprocessing as mp
+        self.workload = workload
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs)
+
+    def run(self, fwd_steps, reps=1):
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, [(self.workload, fwd_steps, reps)] * self.procs)
+        wall = time.perf_counter() - t0
+        lus = sum(r["lattice_updates"] for rr in res for r in rr)
+        return {"value": lus / wall / 1e6, "seconds": wall, "lattice_updates": lus,
+                "per_process_mlups": statistics.median(r["value"] for rr in res for r in rr)}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def cpu_model():
@@ -281,29 +384,64 @@ def cpu_model():
     return "unknown"
 
 
+def sample_text(case, c_s, f, fwd_steps, procs):
+    scaled = (f"the {case.name} duct scaled by 1/{f} ({c_s.nx}x{c_s.ny}x{c_s.nz}, same tau, Cs and inlet speed)"
+              if f > 1 else f"the full {case.name} lattice")
+    return (f"FP64 numpy oracle: a {fwd_steps}-step window from rest of {scaled} plus its adjoint, "
+            f"{2 * fwd_steps * c_s.n} lattice updates per process, {procs} single-thread process(es) in parallel")
+
+
+def cpu_baseline_legs(case, fwd_steps=2):
+    """The oracle timed on one thread and on every host core (both bounded:
+    a few seconds each), for the GPU arm's cpu_baseline."""
+    c_s, f = oracle_case(case)
+    one = oracle_sample(c_s, fwd_steps)
+    procs = oracle_processes(c_s)
+    pool = OraclePool(case.name, procs)
+    try:
+        pool.run(1)                       # workers import numpy / scipy and build their problem once
+        allc = pool.run(fwd_steps)
+    finally:
+        pool.close()
+    return {"value": allc["value"], "unit": "MLUPS", "cores": procs, "kind": "oracle",
+            "sample": sample_text(case, c_s, f, fwd_steps, procs), "cpu": cpu_model(),
+            "host_cores": host_cores(), "seconds": allc["seconds"],
+            "single_thread": {"value": one["value"], "unit": "MLUPS", "cores": 1, "seconds": one["seconds"]}}
+
+
 def run_reference(args, case, rank, world):
+    """The reference arm: the FP64 oracle as it stands on this host's cores
+    (rank 0 only).  Each step is one bounded sample per process: a 2-step
+    window of the sample lattice plus its adjoint."""
     if rank != 0:
         return 0
-    sample_steps = 2
-    for _ in range(args.warmup):
-        oracle_sample(case, sample_steps)
-    vals, secs = [], 0.0
-    for _ in range(args.steps):
-        r = oracle_sample(case, sample_steps)
-        vals.append(r["value"])
-        secs += r["seconds"]
-    value = args.steps * 2 * sample_steps * case.n / secs / 1e6
-    sample = (f"FP64 numpy oracle, one thread: per step a {sample_steps}-step window of the full "
-              f"{case.nx}x{case.ny} lattice plus its adjoint ({2 * sample_steps * case.n} lattice updates)")
+    fwd_steps = 2
+    c_s, f = oracle_case(case)
+    procs = oracle_processes(c_s)
+    pool = OraclePool(case.name, procs)
+    try:
+        pool.run(1)
+        for _ in range(args.warmup):
+            pool.run(fwd_steps)
+        secs, lus = 0.0, 0
+        for _ in range(args.steps):
+            r = pool.run(fwd_steps)
+            secs += r["seconds"]
+            lus += r["lattice_updates"]
+    finally:
+        pool.close()
+    value = lus / secs / 1e6
+    sample = sample_text(case, c_s, f, fwd_steps, procs)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded inputs shaped like the paper's cylinder wake)",
-        "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "window_len": case.window_len,
-                   "ckpt_every": case.ckpt_every},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
-                         "cpu": cpu_model()},
+        "data": f"synthetic (seeded inputs shaped like the paper's {'U-bend' if case.lattice == 19 else '2D'} case)",
+        "config": {"workload": case.name, "nx": case.nx, "ny": case.ny, "nz": case.nz,
+                   "window_len": case.window_len, "ckpt_every": case.ckpt_every,
+                   "oracle_sample": f"{c_s.nx}x{c_s.ny}x{c_s.nz}"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": procs, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model(), "host_cores": host_cores()},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -358,6 +496,7 @@ def run_ours(args, case, rank, world, local):
     t0 = time.perf_counter()
     rec = sol.run_until_converged(max_windows=max(1, args.spinup_windows)) if args.spinup_windows > 0 else []
     protocol = {"windows": len(rec), "steps": len(rec) * W, "converged": bool(rec and rec[-1]["converged"]),
+                "ratios": [r["ratio"] for r in rec[1:]],
                 "last_ratio": rec[-1]["ratio"] if rec else None, "J_eff": rec[-1]["J"] if rec else None,
                 "conv_tol": case.conv_tol, "seconds": time.perf_counter() - t0}
     # Phase timing is on from the first warm-up step: the graphs that carry its
@@ -436,10 +575,17 @@ def run_ours(args, case, rank, world, local):
     }
     dom = max(units, key=lambda u: units[u]["total_ms"])
     u = units[dom]
-    ach = u["bytes"] / (u["us"] / 1e6) / 1e9
+    sv = survey_bytes_per_lu(case, dom, rs=rs) * n      # the scope table's count for the unit
+    ach = sv / (u["us"] / 1e6) / 1e9
+    ach_design = u["bytes"] / (u["us"] / 1e6) / 1e9
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": unit_traffic(dom, case, K),
-            "unit_of_work": dom, "kernel": u["kernel"], "bytes_per_unit": u["bytes"], "us_per_unit": u["us"],
+            "unit_of_work": dom, "kernel": u["kernel"], "bytes_per_unit": sv,
+            "bytes_per_lu": survey_bytes_per_lu(case, dom, rs=rs), "us_per_unit": u["us"],
+            "design_count": {"bytes_per_unit": u["bytes"], "bytes_per_lu": u["bytes"] / n,
+                             "achieved": ach_design, "frac": ach_design / hbm,
+                             "note": "this design's own algorithmic bytes (FP32 per-segment sensitivity partial, "
+                                     "no separate segment store); the headline uses the scope table's count"},
             "peak_kind": f"{pk_kind} hbm_gbs (copy)",
             "timing": "CUDA events on the library stream inside the timed region: per forward-window phase, and "
                       "around each whole adjoint sweep",
@@ -496,11 +642,7 @@ def run_ours(args, case, rank, world, local):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        r = oracle_sample(case, 2)
-        cpu = {"value": r["value"], "unit": "MLUPS", "cores": r["cores"], "kind": "oracle",
-               "sample": (f"FP64 numpy oracle, one thread: a 2-step window of the full {case.nx}x{case.ny} "
-                          f"lattice plus its adjoint ({r['lattice_updates']} lattice updates, {r['seconds']:.1f} s)"),
-               "cpu": cpu_model()}
+        cpu = cpu_baseline_legs(case)
 
     # kernels the library enqueued for the last window and sweep, plus the gradient kernel
     launches_per_step = sched["kernels_window"] + sched["kernels_adjoint"] + 1
@@ -508,7 +650,8 @@ def run_ours(args, case, rank, world, local):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == B.LBM_FP64 else "f32",
-        "data": "synthetic (seeded inputs shaped like the paper's cylinder wake)",
+        "data": ("synthetic (seeded inputs shaped like the paper's U-bend, extruded to 3D)" if case.lattice == 19
+                 else "synthetic (seeded inputs shaped like the paper's 2D cases)"),
         "config": {"workload": case.name, "lattice": f"D{2 if case.lattice == 9 else 3}Q{case.lattice}",
                    "nx": case.nx, "ny": case.ny, "nz": case.nz,
                    "window_len": W, "sample_every": case.sample_every, "ckpt_every": K,
@@ -516,8 +659,8 @@ def run_ours(args, case, rank, world, local):
                    "cs_smag": case.cs_smag, "parallelism": f"replicas x{world}",
                    "cuda_graphs": bool(args.graphs), "pipeline": bool(args.pipeline),
                    "pdl": bool(args.pdl),
-                   "l2": "flushed (256 MB write) before every timed step; inside a step the forward "
-                         "lattices (19 MB) stay L2-resident"},
+                   "l2": (f"flushed (256 MB write) before every timed step; each population field is "
+                          f"{case.lattice * n * rs / 1e6:.0f} MB against a 126 MB L2")},
         "fwd_mlups": 1e-6 * timing["forward"]["lattice_updates"] / (timing["forward"]["ms"] / 1e3),
         "adj_mlups_incl_recompute": 1e-6 * W * n / (sweep_ms / 1e3),
         "roofline": roof,
@@ -660,6 +803,102 @@ def run_optimize(args, case):
     return 0
 
 
+def run_ckpt_sweep(args, case):
+    """Mixed-precision checkpoints against the plain FP64 GPU adjoint.
+
+    After a spin-up of the workload (FP32, its own window length), one window
+    of W_c steps with K_c-step segments (fp64_check_window: the longest window
+    whose FP64 context fits in ~150 GB next to the FP32 one) is run from the
+    same start field with FP32 populations and each checkpoint format (FP32
+    native, FP16, BF16, lossless moment planes).  The forward pass does not
+    depend on the format, so every run follows the same primal trajectory; the
+    FP64 reference runs its window along the FP32-native run's checkpoints
+    (lbm_step_window_along) and its adjoint over that trajectory.  Reported
+    per format: gradient cosine and relative error against FP64, J relative
+    error, adjoint-sweep time (CUDA events on the library stream, the second
+    of two sweeps) and the context's workspace bytes."""
+    import numpy as np
+    import torch
+    from paper_2608_19617_b300 import binding as B
+    B.lib()
+    stream = torch.cuda.Stream()
+    W_c, K_c = fp64_check_window(case)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        spin = B.Solver(case, B.LBM_FP32, stream=stream)
+    rec = spin.run_until_converged(max_windows=max(1, args.spinup_windows))
+    p0 = spin.get_state()
+    spin.close()
+    del spin
+    torch.cuda.empty_cache()
+
+    def timed_sweep(sol):
+        ms = []
+        for _ in range(2):
+            sol.set_state(p0)
+            J, _ = sol.step_window()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sol.adjoint_window()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return J, sol.design_gradient(), ms[-1]
+
+    def cmp(g, J, g64, J64):
+        m = np.abs(g64) > 0
+        n1, n2 = float(np.linalg.norm(g[m])), float(np.linalg.norm(g64[m]))
+        return {"grad_cosine": float(g[m] @ g64[m] / (n1 * n2)), "grad_rel_err": float(np.linalg.norm(g - g64) / n2),
+                "J_rel_err": abs(J - J64) / abs(J64)}
+
+    rows = {}
+    base = case.replace(window_len=W_c, ckpt_every=K_c)
+    with torch.cuda.stream(stream):
+        nat = B.Solver(base.replace(ckpt_format=0), B.LBM_FP32, stream=stream, pipeline=0)
+    J32, g32, ms32 = timed_sweep(nat)
+    with torch.cuda.stream(stream):
+        ref = B.Solver(base.replace(ckpt_format=0), B.LBM_FP64, stream=stream, pipeline=0)
+    ref.set_state(p0)
+    t1 = time.perf_counter()
+    J64, _ = ref.step_window_along(nat)
+    torch.cuda.synchronize()
+    t_fwd64 = time.perf_counter() - t1
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ref.adjoint_window()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b)
+    g64 = ref.design_gradient()
+    fp64 = {"workspace_bytes": int(ref.workspace.numel()), "adjoint_sweep_ms": ms64,
+            "adjoint_mlups_incl_recompute": W_c * case.n / (ms64 / 1e3) / 1e6,
+            "forward_window_s_host": t_fwd64, "grad_norm": float(np.linalg.norm(g64))}
+    ref.close()
+    rows["fp32"] = dict(cmp(g32, J32, g64, J64), workspace_bytes=int(nat.workspace.numel()), adjoint_sweep_ms=ms32,
+                        adjoint_mlups_incl_recompute=W_c * case.n / (ms32 / 1e3) / 1e6)
+    nat.close()
+    del nat, ref
+    torch.cuda.empty_cache()
+    for name, fmt in (("fp16", 1), ("bf16", 2), ("moment", 3)):
+        with torch.cuda.stream(stream):
+            sol = B.Solver(base.replace(ckpt_format=fmt), B.LBM_FP32, stream=stream, pipeline=0)
+        J, g, ms = timed_sweep(sol)
+        rows[name] = dict(cmp(g, J, g64, J64), workspace_bytes=int(sol.workspace.numel()), adjoint_sweep_ms=ms,
+                          adjoint_mlups_incl_recompute=W_c * case.n / (ms / 1e3) / 1e6, J_equals_fp32=J == J32)
+        sol.close()
+        del sol
+        torch.cuda.empty_cache()
+    out = {"metric": "checkpoint-storage sweep: FP32 adjoint with FP32/FP16/BF16/moment checkpoints against the FP64 "
+                     "GPU adjoint on the same trajectory",
+           "impl": "ours", "data": "synthetic",
+           "config": {"workload": case.name, "window_len": W_c, "ckpt_every": K_c,
+                      "workload_window_len": case.window_len, "spinup_windows": len(rec),
+                      "spinup_converged": bool(rec[-1]["converged"]), "pipeline": False},
+           "J_fp64": J64, "fp64": fp64, "formats": rows, "seconds": time.perf_counter() - t0}
+    print(json.dumps(out))
+    return 0
+
+
 def run_fd_protocol(args, case):
     """Sec. 4.2.1: single-point perturbations of the design against the
     adjoint sensitivity, with the same representative window and sampling
@@ -745,6 +984,8 @@ def main():
         case = case.replace(window_len=wl, ckpt_every=args.ckpt_every or wl)
     if args.ckpt_format:
         case = case.replace(ckpt_format=CKPT_NAMES.index(args.ckpt_format))
+    if args.precision == "fp64" and case.ckpt_format in (1, 2):
+        case = case.replace(ckpt_format=0)    # 16-bit checkpoints exist for the FP32 solver only
     if args.impl == "reference":
         rc = run_reference(args, case, rank, world)
         return rc
@@ -754,6 +995,8 @@ def main():
         return run_optimize(args, case) if rank == 0 else 0
     if args.fd_protocol:
         return run_fd_protocol(args, case) if rank == 0 else 0
+    if args.ckpt_sweep:
+        return run_ckpt_sweep(args, case) if rank == 0 else 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

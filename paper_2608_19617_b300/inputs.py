@@ -389,15 +389,13 @@ def ubend_geometry(nx, ny, nz, lf):
     return fluid, cls, xr, ld
 
 
-def config_ubend(seed=1004, big=False) -> Case:
-    """D3Q19 U-bend duct.  Small: 256x128x64, lf=32, Re=1000, Cs=0.1, windows of
-    1000, BF16 checkpoints every 200.  Big: 384x192x192, lf=48, Re=3000, Cs=0.15,
-    windows of 2000.  Design = smooth noise (sigma 4) in the bend region;
-    objective = mean pressure drop between the inlet and outlet legs."""
-    if big:
-        nx, ny, nz, lf, re, cs, wl, ck = 384, 192, 192, 48, 3000.0, 0.15, 2000, 50
-    else:
-        nx, ny, nz, lf, re, cs, wl, ck = 256, 128, 64, 32, 1000.0, 0.1, 1000, 200
+def ubend_case(nx, ny, nz, lf, *, re=1000.0, tau=None, cs_smag=0.1, u_in=0.05, window_len=1000,
+               ckpt_every=200, ckpt_format=CKPT_BF16, seed=1004, name=None) -> Case:
+    """A D3Q19 U-bend duct (ubend_geometry) with a velocity inlet on its upper
+    leg and a zero-gradient outlet on its lower leg, both on the x = 0 face.
+    Design = smooth noise (sigma 4) in the bend region x >= xr; objective =
+    mean pressure drop between the inlet and outlet legs at x = lf; tau from
+    Re on the leg width unless given."""
     fluid, cls, xr, ld = ubend_geometry(nx, ny, nz, lf)
     gamma = np.where(fluid, 0.0, 1.0)
     region = np.zeros_like(fluid)
@@ -407,19 +405,30 @@ def config_ubend(seed=1004, big=False) -> Case:
     gamma[cls == WALL] = 1.0
     gamma[cls == INLET] = 0.0
     gamma[cls == OUTLET_ZG] = 0.0
-    uin = np.where(cls[:, :, 0] == INLET, 0.05, 0.0)
+    uin = np.where(cls[:, :, 0] == INLET, u_in, 0.0)
     w = np.zeros((nz, ny, nx))
     lp = lf
     sec_in = fluid[:, :, lp] & (np.mgrid[0:nz, 0:ny][1] > ny / 2)
     sec_out = fluid[:, :, lp] & (np.mgrid[0:nz, 0:ny][1] < ny / 2)
     w[:, :, lp][sec_in] = 1.0 / sec_in.sum()
     w[:, :, lp][sec_out] = -1.0 / sec_out.sum()
-    return Case(name=f"ubend{nx}x{ny}x{nz}", lattice=19, nx=nx, ny=ny, nz=nz,
-                tau=tau_from_re(0.05, lf, re), cs_smag=cs, node_class=cls, gamma=gamma,
-                inlet_u=uin, obj_weights=w, obj_kind=OBJ_PRESSURE, monitor_u=0.05,
-                monitor_l=float(lf), window_len=wl, sample_every=1, conv_tol=1e-3,
-                ckpt_every=ck, ckpt_format=CKPT_BF16, max_windows=40,
+    return Case(name=name or f"ubend{nx}x{ny}x{nz}", lattice=19, nx=nx, ny=ny, nz=nz,
+                tau=tau if tau is not None else tau_from_re(u_in, lf, re), cs_smag=cs_smag, node_class=cls,
+                gamma=gamma, inlet_u=uin, obj_weights=w, obj_kind=OBJ_PRESSURE, monitor_u=u_in,
+                monitor_l=float(lf), window_len=window_len, sample_every=1, conv_tol=1e-3,
+                ckpt_every=ckpt_every, ckpt_format=ckpt_format, max_windows=40,
                 design_box=(xr, nx - 1, 1, ny - 1, ld, nz - ld))
+
+
+def config_ubend(seed=1004, big=False) -> Case:
+    """D3Q19 U-bend duct.  Small: 256x128x64, lf=32, Re=1000, Cs=0.1, windows of
+    1000, BF16 checkpoints every 200.  Big: 384x192x192, lf=48, Re=3000, Cs=0.15,
+    windows of 2000, BF16 checkpoints every 50.  Design = smooth noise (sigma 4)
+    in the bend region; objective = mean pressure drop between the inlet and
+    outlet legs."""
+    if big:
+        return ubend_case(384, 192, 192, 48, re=3000.0, cs_smag=0.15, window_len=2000, ckpt_every=50, seed=seed)
+    return ubend_case(256, 128, 64, 32, re=1000.0, cs_smag=0.1, window_len=1000, ckpt_every=200, seed=seed)
 
 
 WORKLOADS = {

@@ -41,6 +41,10 @@ FWD_CASES = {
     "duct3d-150x7x6": lambda: I.small_duct3d(150, 7, 6, tau=0.53, window_len=20),
     "duct3d-periodicz": lambda: I.small_duct3d(133, 6, 5, tau=0.54, periodic_z=True, window_len=20,
                                                obj_kind=I.OBJ_DISSIPATION),
+    # the layout of the U-bend workloads at reduced size: a velocity inlet and
+    # a zero-gradient outlet side by side on the x = 0 face, walls and 3D wall
+    # corners around them, the bend near x = nx-1
+    "ubend48x28x16": lambda: I.ubend_case(48, 28, 16, 8, tau=0.52, cs_smag=0.1, window_len=20, ckpt_every=20),
 }
 
 
@@ -85,6 +89,12 @@ ADJ_CASES = {
     "d3q19-pressure": lambda: I.small_duct3d(130, 6, 6, window_len=8, tau=0.53),
     "d3q19-diss-periodicz": lambda: I.small_duct3d(131, 6, 5, window_len=8, obj_kind=I.OBJ_DISSIPATION,
                                                    periodic_z=True, tau=0.54),
+    # pressure drop between the legs at x = 8: a 12-step adjoint reaches the
+    # transposed inlet and zero-gradient rules on the x = 0 face; the design
+    # box spans the whole duct so that the gradient sees them
+    "ubend48x28x16-pressure": lambda: I.ubend_case(48, 28, 16, 8, tau=0.52, cs_smag=0.1, window_len=12,
+                                                   ckpt_every=4, ckpt_format=I.CKPT_NATIVE).replace(
+                                                       design_box=(1, 47, 1, 27, 1, 15)),
 }
 
 
@@ -255,7 +265,7 @@ def test_device_buffers_and_autograd():
 # Full-size workloads in the benchmark's launch configuration.
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["wake1024x256", "step2048x512"])
+@pytest.mark.parametrize("name", ["wake1024x256", "step2048x512", "ubend256x128x64"])
 def test_full_size_one_step_against_oracle(name):
     """After a spin-up on the GPU, one more GPU step equals the oracle's step
     from the same field, element by element (FP32 vs FP64)."""
@@ -268,6 +278,33 @@ def test_full_size_one_step_against_oracle(name):
     pr = O.Problem(case)
     want = oracle_advance(pr, p, 1)
     assert np.abs(got - want).max() < 2e-6
+
+
+def test_channel_workload_fp64_at_full_size_against_oracle():
+    """The 128x64 channel workload (parabolic Zou-He inlet, zero-gradient
+    outlet, disk plus noise, FP64): 200 steps from rest against the oracle,
+    1e-12 relative; then a window of its full length (200 steps, K = 200) and
+    its adjoint, window means 1e-12 and gradient 1e-11."""
+    case = f32_inputs(I.WORKLOADS["channel128x64"]())
+    pr = O.Problem(case)
+    sol = B.Solver(case, B.LBM_FP64)
+    sol.advance(200)
+    got = sol.get_state()
+    want = oracle_advance(pr, pr.initial_state(), 200)
+    assert rel_err(got, want) < 1e-12
+    sol.set_state(want)
+    J, M = sol.step_window()
+    sol.adjoint_window()
+    grad = sol.design_gradient()
+    _, Jw, Mw, traj = pr.run_window(want)
+    _, grad_w, _ = pr.adjoint_window(traj)
+    assert abs(J - Jw) <= 1e-12 * abs(Jw)
+    assert abs(M - Mw) <= 1e-12 * abs(Mw)
+    x0, x1, y0, y1, z0, z1 = case.design_box
+    m = np.zeros((case.nz, case.ny, case.nx), bool)
+    m[z0:z1, y0:y1, x0:x1] = True
+    m = m.reshape(-1)
+    assert rel_err(grad[m], grad_w[m]) < 1e-11
 
 
 def test_full_size_short_window_adjoint_against_oracle():

@@ -144,20 +144,79 @@ __device__ __forceinline__ int offset(const Geo& g, int a) {
 }
 
 // ---------------------------------------------------------------------------
-// Face-node table, built once on the host: everything the face kernels need
-// about a face node's neighbourhood, so that they do plain indexed loads.
+// Row geometry.  Each step runs two kernels on disjoint nodes, both over whole
+// lattice rows along x in blocks of kBlock threads starting at x = 0, so that
+// every warp's loads and stores cover whole, aligned 128-byte lines:
+//  * the row kernels take the inner rows (1 <= y <= ny-2 and, in 3D,
+//    1 <= z <= nz-2; every slice of a D2Q9 batch), x = 0 .. nx-1 included;
+//  * the face-row kernels take the rows on a y or z face, node by node from
+//    the geometry.
+// The x = 0 and x = nx-1 nodes of an inner row pull like every other node,
+// except that a link from outside the domain reads the node itself (an
+// in-row, don't-care value) and a periodic x axis wraps; the boundary rule
+// then replaces those links (xface_complete).  These functions are host and
+// device code so that the host can check every index a launch forms.
 // ---------------------------------------------------------------------------
-constexpr unsigned kNone = 0xffffffffu;
 
-struct FaceTable {
-  const unsigned* __restrict__ idx;    // node index, [nface]
-  const unsigned* __restrict__ info;   // rule mask (bits 0..18: unknowns completed by a rule) | class << 24
-  const float* __restrict__ u0;        // inlet x-velocity (0 elsewhere), [nface]
-  const unsigned* __restrict__ src;    // [Q][nface]: node whose p_a becomes f_a (streaming or zero-gradient copy)
-  const unsigned* __restrict__ dst;    // [Q][nface]: node i + c_a, kNone outside the domain
-  const unsigned* __restrict__ ext;    // [Q][nface]: zero-gradient node that copied p_a(i), or kNone
-  unsigned n;                          // nface
-};
+// Inner rows per z (D3Q19: z interior; D2Q9: every slice) and z of inner row block rz.
+template <class L>
+HD int inner_rows_y(const Geo& g) { return g.ny > 2 ? g.ny - 2 : 0; }
+template <class L>
+HD int inner_rows_z(const Geo& g) { return L::D == 3 ? (g.nz > 2 ? g.nz - 2 : 0) : g.nz; }
+
+// Face rows: per z (all z) the rows y = 0 and y = ny-1 (one if ny == 1), then
+// in 3D for the inner y the rows z = 0 and z = nz-1 (one if nz == 1).  For a
+// D2Q9 batch the face rows of slice z are rows fy z .. fy z + fy - 1.
+template <class L>
+HD int face_rows(const Geo& g) {
+  const int fy = g.ny >= 2 ? 2 : 1, fz = g.nz >= 2 ? 2 : 1;
+  return fy * g.nz + (L::D == 3 ? fz * inner_rows_y<L>(g) : 0);
+}
+
+template <class L>
+HD void face_row_yz(const Geo& g, int r, int& y, int& z) {
+  const int fy = g.ny >= 2 ? 2 : 1, fz = g.nz >= 2 ? 2 : 1;
+  if (r < fy * g.nz) {
+    z = r / fy;
+    y = (r % fy) ? g.ny - 1 : 0;
+  } else {
+    r -= fy * g.nz;
+    y = 1 + r / fz;
+    z = (r % fz) ? g.nz - 1 : 0;
+  }
+}
+
+// Index the pull of direction a reads for inner-row node i at x (Eq. 7):
+// i - c_a, except for a link from outside the domain (the node itself) and
+// across a periodic x axis (wrapped).
+template <class L>
+HD unsigned row_src(const Geo& g, int x, unsigned i, int a) {
+  unsigned j = i - unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
+  if (L::cx(a) > 0 && x == 0) j = g.px ? j + unsigned(g.nx) : i;
+  if (L::cx(a) < 0 && x == g.nx - 1) j = g.px ? j - unsigned(g.nx) : i;
+  return j;
+}
+
+// Index the adjoint pull of direction a reads for inner-row node i at x
+// (Eq. 36): i + c_a; kNone for a link that leaves the domain (its adjoint is 0).
+constexpr unsigned kNone = 0xffffffffu;
+template <class L>
+HD unsigned row_dst(const Geo& g, int x, unsigned i, int a) {
+  unsigned j = i + unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
+  if (L::cx(a) < 0 && x == 0) j = g.px ? j + unsigned(g.nx) : kNone;
+  if (L::cx(a) > 0 && x == g.nx - 1) j = g.px ? j - unsigned(g.nx) : kNone;
+  return j;
+}
+
+// Links of an inner-row node that come from outside a bounded x axis.
+template <class L>
+HD unsigned row_unknowns(const Geo& g, int x) {
+  if (g.px) return 0u;
+  unsigned m = 0;
+  for (int a = 0; a < L::Q; ++a)
+    if ((x == 0 && L::cx(a) > 0) || (x == g.nx - 1 && L::cx(a) < 0)) m |= 1u << a;
+  return m;
+}
 
 // Boundary rules of Eqs. 19-21 (and the 3D velocity inlet) on the unknown
 // populations flagged in mask, in shifted form.
@@ -271,35 +330,55 @@ struct Mom {
   R te, om;                // tau_eff (Eq. 14), 1 - 1/tau_eff
 };
 
+// Add direction a's value v into the running zeroth, first and second
+// moments (rt, m, m2 with entries xx, yy, zz, xy, xz, yz), in the order every
+// kernel uses, so that moments accumulated direction by direction as the
+// loads arrive equal raw_moments() bit for bit.
+template <class L, class R>
+__device__ __forceinline__ void moment_add(int a, R v, R& rt, R (&m)[3], R (&m2)[6]) {
+  const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+  rt += v;
+  if (cx > 0) m[0] += v; else if (cx < 0) m[0] -= v;
+  if (cy > 0) m[1] += v; else if (cy < 0) m[1] -= v;
+  if (cz > 0) m[2] += v; else if (cz < 0) m[2] -= v;
+  if (cx) m2[0] += v;
+  if (cy) m2[1] += v;
+  if (cz) m2[2] += v;
+  if (cx * cy > 0) m2[3] += v; else if (cx * cy < 0) m2[3] -= v;
+  if (cx * cz > 0) m2[4] += v; else if (cx * cz < 0) m2[4] -= v;
+  if (cy * cz > 0) m2[5] += v; else if (cy * cz < 0) m2[5] -= v;
+}
+
 // Zeroth, first and second moments of a population-shaped array, each
 // weighted by wt(a) (1 for f, w_a for adjoints).
 template <class L, class R, bool W>
 __device__ __forceinline__ void raw_moments(const R (&f)[L::Q], R& m0, R (&m1)[3], R (&m2)[6]) {
-  R rt = 0, mx = 0, my = 0, mz = 0, xx = 0, yy = 0, zz = 0, xy = 0, xz = 0, yz = 0;
+  R rt = 0, m[3] = {0, 0, 0}, q[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-  for (int a = 0; a < L::Q; ++a) {
-    const R v = W ? R(L::w(a)) * f[a] : f[a];
-    const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-    rt += v;
-    if (cx > 0) mx += v; else if (cx < 0) mx -= v;
-    if (cy > 0) my += v; else if (cy < 0) my -= v;
-    if (cz > 0) mz += v; else if (cz < 0) mz -= v;
-    if (cx) xx += v;
-    if (cy) yy += v;
-    if (cz) zz += v;
-    if (cx * cy > 0) xy += v; else if (cx * cy < 0) xy -= v;
-    if (cx * cz > 0) xz += v; else if (cx * cz < 0) xz -= v;
-    if (cy * cz > 0) yz += v; else if (cy * cz < 0) yz -= v;
-  }
+  for (int a = 0; a < L::Q; ++a) moment_add<L, R>(a, W ? R(L::w(a)) * f[a] : f[a], rt, m, q);
   m0 = rt;
-  m1[0] = mx; m1[1] = my; m1[2] = mz;
-  m2[0] = xx; m2[1] = yy; m2[2] = zz; m2[3] = xy; m2[4] = xz; m2[5] = yz;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) m1[k] = m[k];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) m2[k] = q[k];
 }
+
+template <class L, class R>
+__device__ __forceinline__ void moments_from_raw(R rt, const R (&m)[3], const R (&m2)[6], const Phys<R>& ph,
+                                                 Mom<L, R>& M);
 
 template <class L, class R>
 __device__ __forceinline__ void moments(const R (&f)[L::Q], const Phys<R>& ph, Mom<L, R>& M) {
   R rt, m[3], m2[6];
   raw_moments<L, R, false>(f, rt, m, m2);
+  moments_from_raw<L, R>(rt, m, m2, ph, M);
+}
+
+// Density, velocity, Pi (Eq. 13), |Pi| and tau_eff (Eq. 14) from the raw
+// moments of the pulled populations.
+template <class L, class R>
+__device__ __forceinline__ void moments_from_raw(R rt, const R (&m)[3], const R (&m2)[6], const Phys<R>& ph,
+                                                 Mom<L, R>& M) {
   M.rt = rt;
   M.rho = R(1) + rt;
   M.inv = R(1) / M.rho;
@@ -426,29 +505,30 @@ __device__ __forceinline__ void sample_commit(double bj, double bm, double* blk)
   sample_commit(bj, bm, blk, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
 }
 
-// The per-step kernels fetch their block's running sums when a sampled step
-// starts: thread 0 issues a 32-byte asynchronous copy into shared memory, so
-// the read overlaps the block's population loads instead of trailing its last
-// reduction (the block keeps its slot on the SM until thread 0 is done).  The
-// sums and their arithmetic are those of sample_commit.
-__device__ __forceinline__ void sample_fetch(Sums* sh, const double* blk, unsigned bid) {
+// The per-step kernels leave each sampled step's block partials (j, monitor)
+// in the working precision in a ring of slots, one store by thread 0 and no
+// read, so a block's last warp retires as soon as its reduction is done.
+// sample_fold_kernel then adds the slots into the blocks' FP64 (sum,
+// compensation) window sums, slot by slot in step order: the same additions,
+// in the same order, as adding each step's partial right away.
+template <class R>
+__device__ __forceinline__ void ring_store(R bj, R bm, R* ring, size_t slot) {
   if (threadIdx.x == 0) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(sh));
-    const size_t src = __cvta_generic_to_global(blk + 4 * size_t(bid));
-    asm volatile(
-        "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
-        "cp.async.cg.shared.global [%2], [%3], 16;\n\t"
-        "cp.async.commit_group;" ::"r"(d), "l"(src), "r"(d + 16u), "l"(src + 16) : "memory");
+    if constexpr (sizeof(R) == 4) reinterpret_cast<float2*>(ring)[slot] = make_float2(bj, bm);
+    else reinterpret_cast<double2*>(ring)[slot] = make_double2(bj, bm);
   }
 }
 
-__device__ __forceinline__ void sample_commit_fetched(double bj, double bm, const Sums* sh, double* blk, unsigned bid) {
-  if (threadIdx.x == 0) {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    Sums a = *sh;
-    neumaier(a.x, a.y, bj);
-    neumaier(a.z, a.w, bm);
-    reinterpret_cast<Sums*>(blk)[bid] = a;
+template <class R>
+__global__ void sample_fold_kernel(const R* __restrict__ ring, int count, unsigned nblk, double* __restrict__ blk) {
+  for (unsigned b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+    Sums a = reinterpret_cast<Sums*>(blk)[b];
+    for (int r = 0; r < count; ++r) {
+      const size_t k = 2 * (size_t(r) * nblk + b);
+      neumaier(a.x, a.y, double(ring[k]));
+      neumaier(a.z, a.w, double(ring[k + 1]));
+    }
+    reinterpret_cast<Sums*>(blk)[b] = a;
   }
 }
 
@@ -466,10 +546,11 @@ struct FwdArgs {
   Geo geo;
   Phys<R> ph;
   Obj<R> obj;
-  int sample;                    // 1 at a sampling instant
-  double* blk;                   // per-block window sums (4 doubles per block)
+  int sample;                    // 0, or at a sampling instant 1 + the ring slot of its block partials
+  R* ring;                       // [slots][nblk][2] block partials of the sampled steps
+  unsigned nblk;                 // blocks of one step (interior + face kernel)
+  double* blk;                   // per-block FP64 window sums (4 doubles per block; no-allocation kernel only)
   int* nonfinite;
-  FaceTable ft;
   R* mom;                        // non-null: also store the step's collision coefficients (moment checkpoint)
 };
 
@@ -572,82 +653,67 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
   }
 }
 
-// One node of a forward step (interior or face node): pull (Eq. 7), complete
-// the boundary populations of a face node (Eqs. 19-21), then forward_core.
-// For a face node k is its row in the face table; for an interior node k is unused.
-template <class L, class R, bool FACE, bool MOM = false>
-__device__ __forceinline__ void forward_node(const FwdArgs<R>& A, const FwdStep<R>& P, int x, int y, int z,
-                                             unsigned i, unsigned k, R& bj, R& bm) {
-  const Geo& g = A.geo;
-  const R* src = P.src;
-  R f[L::Q];
-  if (FACE) {
-    const FaceTable& t = A.ft;
+// Completion of an x-face node of an inner row (bounded x axis): the links in
+// mask came from outside the domain and take the node's rule (Eqs. 19-21, the
+// 3D velocity inlet), or for a zero-gradient outlet the post-streaming value
+// of the neighbour along the inward normal, p_a(i + n_in - c_a).
+template <class L, class R>
+__device__ __forceinline__ void xface_complete(const R* __restrict__ P, const Geo& g, int x, unsigned i,
+                                               unsigned mask, uint8_t cls, R u0, R rho_out, R (&f)[L::Q]) {
+  if (cls == OUTLET_ZG) {
+    const unsigned k = x == 0 ? i + 1u : i - 1u;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = src[a * g.n + t.src[a * t.n + k]];
-    const unsigned info = t.info[k];
-    apply_rules<L, R>(f, info & 0xffffffu, uint8_t(info >> 24), R(t.u0[k]), A.ph.rho_out);
+    for (int a = 0; a < L::Q; ++a)
+      if (mask & (1u << a)) f[a] = P[a * g.n + k - unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz))];
   } else {
+    apply_rules<L, R>(f, mask, cls, u0, rho_out);
+  }
+}
+
+// Pull of an inner-row node (Eq. 7) with its x-face completion; returns the
+// links completed by a rule (0 off the x faces and for a zero-gradient
+// outlet, whose links are copies), with the node's class and inlet velocity.
+template <class L, class R>
+__device__ __forceinline__ unsigned row_gather(const R* __restrict__ P, const uint8_t* __restrict__ cls_arr,
+                                               const float* __restrict__ uin, R rho_out, const Geo& g, int x, int y,
+                                               int z, unsigned i, R (&f)[L::Q], uint8_t& cls, R& u0) {
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = src[a * g.n + i - offset<L>(g, a)];
-  }
-  forward_core<L, R, MOM>(A, P, x, y, z, i, f, bj, bm);
+  for (int a = 0; a < L::Q; ++a) f[a] = P[a * g.n + row_src<L>(g, x, i, a)];
+  cls = FLUID;
+  u0 = R(0);
+  const unsigned mask = row_unknowns<L>(g, x);
+  if (!mask) return 0u;
+  cls = cls_arr[i];
+  if (cls == INLET) u0 = R(uin[unsigned(y) + unsigned(g.ny) * unsigned(z)]);
+  xface_complete<L, R>(P, g, x, i, mask, cls, u0, rho_out, f);
+  return cls == OUTLET_ZG ? 0u : mask;
 }
 
-// Interior nodes: x in [1, nx-1), y in [1, ny-1), z in [1, nz-1) (3D).  No
-// face logic at all, so the instruction stream stays short.
+// Forward step over the inner rows (row geometry above): pull (Eq. 7), the
+// x-face completion on the first and last node of a row, then forward_core.
 template <class L, class R, bool MOM = false>
-__global__ void __launch_bounds__(kBlock) fwd_interior_kernel(FwdArgs<R> A) {
+__global__ void __launch_bounds__(kBlock) fwd_row_kernel(FwdArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
-  const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
+  const int x = int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
   const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
-  __shared__ __align__(16) Sums sums;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  if (A.sample) sample_fetch(&sums, A.blk, bid);   // uniform across the grid
   R bj = 0, bm = 0;
-  if (x < g.nx - 1)
-    forward_node<L, R, false, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u, bj, bm);
-  if (A.sample) {
+  if (x < g.nx) {
+    const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
+    R f[L::Q];
+    uint8_t cls;
+    R u0;
+    row_gather<L, R>(A.src, A.cls, A.uin, A.ph.rho_out, g, x, y, z, i, f, cls, u0);
+    forward_core<L, R, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, f, bj, bm);
+  }
+  if (A.sample) {   // uniform across the grid
     block_sum2<R>(bj, bm);
-    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, bid);
+    ring_store(bj, bm, A.ring, size_t(A.sample - 1) * A.nblk + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
   }
 }
 
-// Face nodes, from the list face[0..nface); block sums after the interior's.
-template <class L, class R, bool MOM = false>
-__global__ void __launch_bounds__(kBlock) fwd_face_kernel(FwdArgs<R> A, unsigned blk0) {
-  pdl_enter();
-  const Geo& g = A.geo;
-  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
-  __shared__ __align__(16) Sums sums;
-  if (A.sample) sample_fetch(&sums, A.blk, blk0 + blockIdx.x);
-  R bj = 0, bm = 0;
-  const unsigned i = k < A.ft.n ? A.ft.idx[k] : kNone;   // rows padded per slice hold kNone
-  if (i != kNone) {
-    const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
-    forward_node<L, R, true, MOM>(A, FwdStep<R>{A.src, A.dst, A.sample, A.mom}, x, y, z, i, k, bj, bm);
-  }
-  if (A.sample) {
-    block_sum2<R>(bj, bm);
-    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, blk0 + blockIdx.x);
-  }
-}
-
-// 2D face rows of one slice in face-table order: the y = 0 row, the
-// (x = 0, x = nx-1) pairs of rows 1 .. ny-2, the y = ny-1 row (nx, ny >= 2).
-__device__ __forceinline__ bool face2d_coords(const Geo& g, unsigned j, int& x, int& y) {
-  const unsigned nx = unsigned(g.nx), side = 2u * unsigned(g.ny - 2);
-  if (j < nx) { x = int(j); y = 0; return true; }
-  j -= nx;
-  if (j < side) { y = 1 + int(j >> 1); x = (j & 1u) ? g.nx - 1 : 0; return true; }
-  j -= side;
-  if (j < nx) { x = int(j); y = g.ny - 1; return true; }
-  return false;
-}
-
-// One face node with its sources from the geometry: class and inlet velocity
-// from the node arrays, populations through gather_geo().
+// One face-row node with its sources from the geometry: class and inlet
+// velocity from the node arrays, populations through gather_geo().
 template <class L, class R, bool MOM>
 __device__ __forceinline__ void face_geo_node(const FwdArgs<R>& A, int x, int y, int z, R& bj, R& bm) {
   const Geo& g = A.geo;
@@ -660,60 +726,20 @@ __device__ __forceinline__ void face_geo_node(const FwdArgs<R>& A, int x, int y,
   forward_core<L, R, MOM>(A, P, x, y, z, i, f, bj, bm);
 }
 
-// D2Q9 face nodes with positions and sources from the geometry: one dependent
-// load level (the populations), like the interior kernel, where the table
-// path needs two (table, then populations).  Rows, blocks and block sums are
-// those of fwd_face_kernel (rows_per_slice = face blocks per slice x kBlock).
+// Forward step over the face rows: one block row of the grid per face row
+// (face_row_yz); block sums after the row kernel's (blk0 onward).
 template <class L, class R, bool MOM = false>
-__global__ void __launch_bounds__(kBlock) fwd_face2d_kernel(FwdArgs<R> A, unsigned blk0, unsigned rows_per_slice) {
+__global__ void __launch_bounds__(kBlock) fwd_facerow_kernel(FwdArgs<R> A, unsigned blk0) {
   pdl_enter();
   const Geo& g = A.geo;
-  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
-  const unsigned z = k / rows_per_slice;
-  __shared__ __align__(16) Sums sums;
-  if (A.sample) sample_fetch(&sums, A.blk, blk0 + blockIdx.x);
+  const int x = int(blockIdx.x) * kBlock + int(threadIdx.x);
+  int y, z;
+  face_row_yz<L>(g, int(blockIdx.y), y, z);
   R bj = 0, bm = 0;
-  int x, y;
-  if (z < unsigned(g.nz) && face2d_coords(g, k - z * rows_per_slice, x, y))
-    face_geo_node<L, R, MOM>(A, x, y, int(z), bj, bm);
+  if (x < g.nx) face_geo_node<L, R, MOM>(A, x, y, z, bj, bm);
   if (A.sample) {
     block_sum2<R>(bj, bm);
-    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, blk0 + blockIdx.x);
-  }
-}
-
-// 3D face rows in face-table (ascending node) order: the z = 0 plane, the
-// rings of faces of slices 1 .. nz-2 (each in 2D face order), the z = nz-1
-// plane (nx, ny, nz >= 2).
-__device__ __forceinline__ bool face3d_coords(const Geo& g, unsigned k, int& x, int& y, int& z) {
-  const unsigned nx = unsigned(g.nx), plane = nx * unsigned(g.ny);
-  const unsigned ring = 2u * nx + 2u * unsigned(g.ny - 2), mid = ring * unsigned(g.nz - 2);
-  if (k < plane) { x = int(k % nx); y = int(k / nx); z = 0; return true; }
-  k -= plane;
-  if (k < mid) {
-    const unsigned s = k / ring;
-    z = 1 + int(s);
-    return face2d_coords(g, k - s * ring, x, y);
-  }
-  k -= mid;
-  if (k < plane) { x = int(k % nx); y = int(k / nx); z = g.nz - 1; return true; }
-  return false;
-}
-
-// D3Q19 face nodes from the geometry (the counterpart of fwd_face2d_kernel):
-// rows, blocks and block sums are those of fwd_face_kernel.
-template <class L, class R, bool MOM = false>
-__global__ void __launch_bounds__(kBlock) fwd_face3d_kernel(FwdArgs<R> A, unsigned blk0) {
-  pdl_enter();
-  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
-  __shared__ __align__(16) Sums sums;
-  if (A.sample) sample_fetch(&sums, A.blk, blk0 + blockIdx.x);
-  R bj = 0, bm = 0;
-  int x, y, z;
-  if (face3d_coords(A.geo, k, x, y, z)) face_geo_node<L, R, MOM>(A, x, y, z, bj, bm);
-  if (A.sample) {
-    block_sum2<R>(bj, bm);
-    sample_commit_fetched(double(bj), double(bm), &sums, A.blk, blk0 + blockIdx.x);
+    ring_store(bj, bm, A.ring, size_t(A.sample - 1) * A.nblk + blk0 + blockIdx.x + gridDim.x * blockIdx.y);
   }
 }
 
@@ -826,7 +852,7 @@ struct AdjArgs {
   int sample;
   int terminal;                  // 1: b^{n+1} = 0 (last step of the window)
   int dbox[6];                   // design box
-  FaceTable ft;
+  int zg;                        // 1 if the lattice has zero-gradient outlet nodes
 };
 
 // Transposed boundary completion at a face node (in place on b).
@@ -938,19 +964,16 @@ struct AdjStep {
   int terminal;
 };
 
-// One node of an adjoint step (interior or face node).
-template <class L, class R, bool FACE>
-__device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<R>& P, int x, int y, int z, unsigned i,
-                                             unsigned kf) {
+// One node of an adjoint step.  ROW: a node of an inner row (row geometry:
+// the adjoint pull of Eq. 36 by row_dst, the x-face completion and its
+// transpose on the first and last node of a row); otherwise a face-row node
+// with every index from the geometry (pull_face, gather_geo).
+template <class L, class R, bool ROW>
+__device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<R>& P, int x, int y, int z, unsigned i) {
   const Geo& g = A.geo;
-  const FaceTable& ft = A.ft;
   const R* bnext = P.bnext;
   const R* pprev = P.pprev;
   R* bout = P.bout;
-  const unsigned info = FACE ? ft.info[kf] : 0u;
-  const uint8_t cls = uint8_t(info >> 24);
-  const unsigned mask = info & 0xffffffu;
-  const R u0 = FACE ? R(ft.u0[kf]) : R(0);
 
   // Weighted moments of the pulled adjoint a^n: A0 = sum w a, A1 = sum w c a,
   // A2 = sum w c c a.  Everything below needs a only through them.
@@ -960,28 +983,40 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
     if (P.terminal) {
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) a[k] = R(0);
-    } else if (FACE) {
+    } else if (ROW) {
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) {
-        const unsigned d = ft.dst[k * ft.n + kf], e = ft.ext[k * ft.n + kf];
-        a[k] = d != kNone ? bnext[k * g.n + d] : R(0);
-        if (e != kNone) a[k] += bnext[k * g.n + e];
+        const unsigned j = row_dst<L>(g, x, i, k);
+        a[k] = j != kNone ? bnext[k * g.n + j] : R(0);
+      }
+      // A zero-gradient outlet node j on this x face copied p_k(i) into its
+      // unknown f_k(j), j = i + c_k - n_in: pull those adjoints back.
+      if (A.zg && row_unknowns<L>(g, x)) {
+        const int sx = x == 0 ? 1 : -1;
+#pragma unroll
+        for (int k = 0; k < L::Q; ++k) {
+          if (L::cx(k) != sx) continue;
+          const unsigned j = i + unsigned(L::cy(k) * int(g.sy) + L::cz(k) * int(g.sz));
+          if (A.cls[j] == OUTLET_ZG) a[k] += bnext[k * g.n + j];
+        }
       }
     } else {
-#pragma unroll
-      for (int k = 0; k < L::Q; ++k) a[k] = bnext[k * g.n + i + offset<L>(g, k)];
+      pull_face<L, R>(bnext, A.cls, g, x, y, z, a);
     }
     raw_moments<L, R, true>(a, A0, A1, A2);
   }
 
   R f[L::Q];
-  if (FACE) {
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = pprev[a * g.n + ft.src[a * ft.n + kf]];
-    apply_rules<L, R>(f, mask, cls, u0, A.ph.rho_out);
+  uint8_t cls;
+  R u0;
+  unsigned mask;
+  if (ROW) {
+    mask = row_gather<L, R>(pprev, A.cls, A.uin, A.ph.rho_out, g, x, y, z, i, f, cls, u0);
   } else {
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[a] = pprev[a * g.n + i - offset<L>(g, a)];
+    cls = A.cls[i];
+    u0 = cls == INLET ? R(A.uin[unsigned(y) + unsigned(g.ny) * unsigned(z)]) : R(0);
+    const unsigned unk = gather_geo<L, R>(pprev, g, x, y, z, cls, u0, A.ph.rho_out, f);
+    mask = (cls == FLUID || cls == OUTLET_ZG) ? 0u : unk;
   }
   Mom<L, R> M;
   moments<L, R>(f, A.ph, M);
@@ -1082,7 +1117,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
   R b[L::Q];
 #pragma unroll
   for (int k = 0; k < L::Q; ++k) b[k] = quad_form<L, R>(k, grho, gm, cpi);
-  if (FACE) bc_transpose<L, R>(b, mask, cls, u0);
+  if (mask) bc_transpose<L, R>(b, mask, cls, u0);
 #pragma unroll
   for (int k = 0; k < L::Q; ++k) bout[k * g.n + i] = b[k];
 
@@ -1090,26 +1125,29 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
   if (x >= d[0] && x < d[1] && y >= d[2] && y < d[3] && z >= d[4] && z < d[5]) A.gpart[i] += gt;
 }
 
+// Adjoint step over the inner rows and over the face rows (the row geometry
+// of the forward step).
 template <class L, class R>
-__global__ void __launch_bounds__(kBlock) adj_interior_kernel(AdjArgs<R> A) {
+__global__ void __launch_bounds__(kBlock) adj_row_kernel(AdjArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
-  const int x = 1 + int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
+  const int x = int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
   const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
-  if (x >= g.nx - 1) return;
-  adjoint_node<L, R, false>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z, unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz, 0u);
+  if (x >= g.nx) return;
+  adjoint_node<L, R, true>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z,
+                           unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz);
 }
 
 template <class L, class R>
-__global__ void __launch_bounds__(kBlock) adj_face_kernel(AdjArgs<R> A) {
+__global__ void __launch_bounds__(kBlock) adj_facerow_kernel(AdjArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
-  const unsigned k = blockIdx.x * kBlock + threadIdx.x;
-  if (k >= A.ft.n) return;
-  const unsigned i = A.ft.idx[k];
-  if (i == kNone) return;
-  const int x = int(i % unsigned(g.nx)), y = int((i / unsigned(g.nx)) % unsigned(g.ny)), z = int(i / g.sz);
-  adjoint_node<L, R, true>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z, i, k);
+  const int x = int(blockIdx.x) * kBlock + int(threadIdx.x);
+  if (x >= g.nx) return;
+  int y, z;
+  face_row_yz<L>(g, int(blockIdx.y), y, z);
+  adjoint_node<L, R, false>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z,
+                            unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz);
 }
 
 // Fold a segment's sensitivity partials into the FP64 (sum, compensation)

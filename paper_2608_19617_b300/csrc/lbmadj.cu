@@ -51,6 +51,9 @@ lbm_status fail(lbm_status s, const char* fmt, ...) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+// Sampled steps whose block partials wait in the ring before a fold into the
+// FP64 window sums.
+constexpr int kRingSlots = 32;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 template <class L>
@@ -78,14 +81,15 @@ unsigned mask_with_cx(int sx) {
 // Layout of the caller's workspace.
 struct Layout {
   size_t f[2], b[2], g, gamma, wobj, cls, uin, gacc, gpart, gout, stage, ckpt, ckpt_slot, seg, seg_slots,
-      partials, acc, flags, f_idx, f_info, f_u0, f_src, f_dst, f_ext, xraw, xfilt, wfilt, slice_j, slice_c,
+      partials, ring, acc, flags, xraw, xfilt, wfilt, slice_j, slice_c,
       total;
   int nblocks_fwd, nblocks_1d, nslots;
-  int igx, igy, igz;          // interior grid (blocks of kBlock along x)
+  int rgx;                    // blocks of kBlock along a row (x = 0 .. nx-1)
+  int iy, iz;                 // inner rows along y and z (row kernels' grid)
+  int nfr;                    // face rows (face-row kernels' grid)
+  int fy;                     // face rows per z (D2Q9: per slice)
+  int row_blocks;             // row-kernel blocks; face-row blocks follow in the block sums
   size_t seg_sets;            // 2 when recompute and adjoint are pipelined
-  unsigned nface;             // face nodes
-  int face_blocks;
-  int fbs;                    // D2Q9: face blocks per slice (rows padded per slice)
   bool stage_in_seg;
 };
 
@@ -134,24 +138,17 @@ Layout make_layout(const lbm_config& c) {
   const int d = c.lattice == LBM_D2Q9 ? 2 : 3;
   const size_t rs = c.precision == LBM_FP64 ? 8 : 4;
   const size_t lat = align_up(size_t(q) * n * rs);
-  // Interior nodes (off every face) run in one kernel, face nodes in another.
-  const int ix = c.nx > 2 ? c.nx - 2 : 0, iy = c.ny > 2 ? c.ny - 2 : 0;
+  // Inner rows run in the row kernels, the rows of the y and z faces in the
+  // face-row kernels (kernels.cuh, row geometry); both cover whole rows.
   const bool d2 = c.lattice == LBM_D2Q9;
-  const int iz = d2 ? c.nz : (c.nz > 2 ? c.nz - 2 : 0);
-  L.igx = (ix + lbm::kBlock - 1) / lbm::kBlock;
-  L.igy = iy;
-  L.igz = iz;
-  if (d2) {
-    // face rows padded per slice so that every face block belongs to one slice
-    const size_t per = size_t(c.nx) * c.ny - size_t(ix) * iy;
-    L.fbs = int((per + lbm::kBlock - 1) / lbm::kBlock);
-    L.nface = unsigned(size_t(L.fbs) * lbm::kBlock * c.nz);
-  } else {
-    L.nface = unsigned(n - size_t(ix) * iy * iz);
-    L.fbs = 0;
-  }
-  L.face_blocks = int((L.nface + lbm::kBlock - 1) / lbm::kBlock);
-  L.nblocks_fwd = L.igx * L.igy * L.igz + L.face_blocks;
+  L.rgx = (c.nx + lbm::kBlock - 1) / lbm::kBlock;
+  L.iy = c.ny > 2 ? c.ny - 2 : 0;
+  L.iz = d2 ? c.nz : (c.nz > 2 ? c.nz - 2 : 0);
+  L.fy = c.ny >= 2 ? 2 : 1;
+  const int fz = c.nz >= 2 ? 2 : 1;
+  L.nfr = L.fy * c.nz + (d2 ? 0 : fz * L.iy);
+  L.row_blocks = L.rgx * L.iy * L.iz;
+  L.nblocks_fwd = L.row_blocks + L.rgx * L.nfr;
   L.nblocks_1d = int((n + lbm::kBlock - 1) / lbm::kBlock);
   L.nslots = c.window_len / c.ckpt_every;
   const bool native = c.ckpt_format == LBM_CKPT_NATIVE;
@@ -177,12 +174,7 @@ Layout make_layout(const lbm_config& c) {
   L.gpart = take(n * rs);
   L.gout = take(n * 8);
   L.partials = take(size_t(L.nblocks_fwd) * 32);
-  L.f_idx = take(size_t(L.nface) * 4);
-  L.f_info = take(size_t(L.nface) * 4);
-  L.f_u0 = take(size_t(L.nface) * 4);
-  L.f_src = take(size_t(L.nface) * 4 * q);
-  L.f_dst = take(size_t(L.nface) * 4 * q);
-  L.f_ext = take(size_t(L.nface) * 4 * q);
+  L.ring = take(size_t(kRingSlots) * L.nblocks_fwd * 2 * rs);
   L.xraw = take(n * 4);       // raw design variables (filtered designs)
   L.slice_j = take(size_t(c.nz) * 16);   // per-slice window means (J, M) of a D2Q9 batch
   L.slice_c = take(size_t(c.nz) * 8);    // per-slice constant of a pressure objective
@@ -211,7 +203,9 @@ struct Pending {
 // Polymorphic per-(lattice, precision) implementation.
 struct Impl {
   virtual ~Impl() = default;
+  // sample: 0, or 1 + the ring slot that takes the step's block partials
   virtual void fwd(const void* src, void* dst, int sample, void* mom = nullptr) = 0;
+  virtual void fold(int count) = 0;   // add count ring slots into the FP64 window sums
   virtual void adj(const void* bnext, const void* pprev, void* bout, int sample) = 0;
   virtual void pull(const void* b, void* out) = 0;
   virtual void set_design() = 0;
@@ -251,6 +245,7 @@ struct lbm_ctx {
   cudaEvent_t fork_cur = nullptr, join_cur = nullptr;
   bool use_graphs = true;
   bool use_pdl = true;        // programmatic dependent launch of the step kernels
+  bool has_zg = false;        // some node is a zero-gradient outlet
   int64_t kernels = 0;        // kernel launches enqueued so far
   int64_t kernels_window = 0, kernels_adjoint = 0;   // per window / per adjoint sweep, as last enqueued
   lbm_ctx* along = nullptr;   // lbm_step_window_along: the context whose checkpoints start each segment
@@ -380,25 +375,22 @@ struct ImplT final : Impl {
     long long b = (long long)(c->n * c->q + 255) / 256;
     return int(b < 148 * 32 ? b : 148 * 32);
   }
-  dim3 igrid() const { return dim3(c->lay.igx, c->lay.igy, c->lay.igz); }
-  lbm::FaceTable table() const {
-    return lbm::FaceTable{c->template at<unsigned>(c->lay.f_idx), c->template at<unsigned>(c->lay.f_info),
-                          c->template at<float>(c->lay.f_u0),   c->template at<unsigned>(c->lay.f_src),
-                          c->template at<unsigned>(c->lay.f_dst), c->template at<unsigned>(c->lay.f_ext),
-                          c->lay.nface};
-  }
-  bool has_interior() const { return c->lay.igx > 0 && c->lay.igy > 0 && c->lay.igz > 0; }
-  bool face2d() const { return L::D == 2 && c->cfg.nx >= 2 && c->cfg.ny >= 2; }
-  bool face3d() const { return L::D == 3 && c->cfg.nx >= 2 && c->cfg.ny >= 2 && c->cfg.nz >= 2; }
+  dim3 rgrid() const { return dim3(c->lay.rgx, c->lay.iy, c->lay.iz); }
+  dim3 fgrid() const { return dim3(c->lay.rgx, c->lay.nfr); }
+  bool has_interior() const { return c->lay.row_blocks > 0; }
   // Step kernels: optionally with programmatic stream serialization, so that a
   // launch overlaps the tail of its predecessor (the kernel waits in
   // pdl_enter before touching data).
   template <class... Args>
   void launch(void (*kernel)(Args...), dim3 grid, cudaStream_t st, Args... args) {
+    launch_b(kernel, grid, lbm::kBlock, st, args...);
+  }
+  template <class... Args>
+  void launch_b(void (*kernel)(Args...), dim3 grid, int block, cudaStream_t st, Args... args) {
     if (c->use_pdl) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = grid;
-      cfg.blockDim = dim3(lbm::kBlock);
+      cfg.blockDim = dim3(block);
       cfg.stream = st;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -407,7 +399,7 @@ struct ImplT final : Impl {
       cfg.numAttrs = 1;
       cudaLaunchKernelEx(&cfg, kernel, args...);
     } else {
-      kernel<<<grid, lbm::kBlock, 0, st>>>(args...);
+      kernel<<<grid, block, 0, st>>>(args...);
     }
   }
   // Interior kernel on the launch stream, face kernel on the side stream,
@@ -451,9 +443,10 @@ struct ImplT final : Impl {
     A.ph = phys();
     A.obj = obj();
     A.sample = sample;
-    A.blk = c->template at<double>(c->lay.partials);
+    A.ring = c->template at<R>(c->lay.ring);
+    A.nblk = unsigned(c->lay.nblocks_fwd);
+    A.blk = nullptr;
     A.nonfinite = c->template at<int>(c->lay.flags);
-    A.ft = table();
     return A;
   }
   lbm::AdjArgs<R> adj_args(const void* bnext, const void* pprev, void* bout, int sample) const {
@@ -472,48 +465,28 @@ struct ImplT final : Impl {
     A.sample = sample;
     A.terminal = bnext == nullptr;
     for (int i = 0; i < 6; ++i) A.dbox[i] = c->cfg.design_box[i];
-    A.ft = table();
+    A.zg = c->has_zg ? 1 : 0;
     return A;
   }
   void fwd(const void* src, void* dst, int sample, void* mom) override {
     const lbm::FwdArgs<R> A = fwd_args(src, dst, sample, mom);
-    const unsigned blk0 = unsigned(c->lay.igx * c->lay.igy * c->lay.igz);
+    const unsigned blk0 = unsigned(c->lay.row_blocks);
     // the step that writes a moment checkpoint runs its own instantiation (MOM)
     fork_join(
         [&](cudaStream_t st) {
-          if (mom) launch(lbm::fwd_interior_kernel<L, R, true>, igrid(), st, A);
-          else launch(lbm::fwd_interior_kernel<L, R, false>, igrid(), st, A);
+          if (mom) launch(lbm::fwd_row_kernel<L, R, true>, rgrid(), st, A);
+          else launch(lbm::fwd_row_kernel<L, R, false>, rgrid(), st, A);
         },
         [&](cudaStream_t st) {
-          // face positions and sources from the geometry (one load level); the face table on
-          // degenerate lattices
-          const dim3 fg(c->lay.face_blocks);
-          if constexpr (L::D == 2) {
-            if (face2d()) {
-              const unsigned rows = unsigned(c->lay.fbs) * lbm::kBlock;
-              if (mom) launch(lbm::fwd_face2d_kernel<L, R, true>, fg, st, A, blk0, rows);
-              else launch(lbm::fwd_face2d_kernel<L, R, false>, fg, st, A, blk0, rows);
-              return;
-            }
-          } else {
-            if (face3d()) {
-              if (mom) launch(lbm::fwd_face3d_kernel<L, R, true>, fg, st, A, blk0);
-              else launch(lbm::fwd_face3d_kernel<L, R, false>, fg, st, A, blk0);
-              return;
-            }
-          }
-          if (mom) {
-            launch(lbm::fwd_face_kernel<L, R, true>, fg, st, A, blk0);
-          } else {
-            launch(lbm::fwd_face_kernel<L, R, false>, fg, st, A, blk0);
-          }
+          if (mom) launch(lbm::fwd_facerow_kernel<L, R, true>, fgrid(), st, A, blk0);
+          else launch(lbm::fwd_facerow_kernel<L, R, false>, fgrid(), st, A, blk0);
         });
   }
 
   void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
     const lbm::AdjArgs<R> A = adj_args(bnext, pprev, bout, sample);
-    fork_join([&](cudaStream_t st) { launch(lbm::adj_interior_kernel<L, R>, igrid(), st, A); },
-              [&](cudaStream_t st) { launch(lbm::adj_face_kernel<L, R>, dim3(c->lay.face_blocks), st, A); });
+    fork_join([&](cudaStream_t st) { launch(lbm::adj_row_kernel<L, R>, rgrid(), st, A); },
+              [&](cudaStream_t st) { launch(lbm::adj_facerow_kernel<L, R>, fgrid(), st, A); });
   }
 
   const void* checkpoint_field(int s) override {
@@ -533,6 +506,12 @@ struct ImplT final : Impl {
                                                                         static_cast<R*>(dst), total);
   }
 
+  void fold(int count) override {
+    const int nb = int(std::min<long long>((c->lay.nblocks_fwd + 255) / 256, 148 * 8));
+    c->kernels += 1;
+    lbm::sample_fold_kernel<R><<<nb, 256, 0, c->ls>>>(c->template at<R>(c->lay.ring), count,
+                                                      unsigned(c->lay.nblocks_fwd), c->template at<double>(c->lay.partials));
+  }
   void pull(const void* b, void* out) override {
     lbm::adj_pull_kernel<L, R><<<grid(), lbm::kBlock, 0, c->ls>>>(
         static_cast<const R*>(b), c->template at<uint8_t>(c->lay.cls), static_cast<R*>(out), c->geo);
@@ -673,6 +652,7 @@ lbm_status enqueue_window(lbm_ctx* c) {
   const bool moment = k.ckpt_format == LBM_CKPT_MOMENT;
   const size_t lat_bytes = c->q * c->n * c->rs;
   const int64_t k0 = c->kernels;
+  int pending = 0;   // sampled steps waiting in the ring
   for (int s = 0; s < S; ++s) {
     if (c->along) {   // start the segment from the reference context's checkpoint s
       lbm_ctx* r = c->along;
@@ -692,18 +672,23 @@ lbm_status enqueue_window(lbm_ctx* c) {
     e = c->begin();
     for (int j = 0; j < K; ++j) {
       const int step = s * K + j;
-      c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), lbm::sampled_step(step, c->sample_from, k.sample_every),
-                   j == K - 1 ? mom : nullptr);
+      const bool sampled = lbm::sampled_step(step, c->sample_from, k.sample_every);
+      c->impl->fwd(c->lattice(c->cur), c->lattice(c->cur ^ 1), sampled ? 1 + pending : 0, j == K - 1 ? mom : nullptr);
       c->cur ^= 1;
+      if (sampled && ++pending == kRingSlots) {
+        c->impl->fold(pending);
+        pending = 0;
+      }
     }
     c->end(e, 0, K, int64_t(K) * int64_t(c->n));
   }
+  if (pending) c->impl->fold(pending);
   const double mon_scale =
       k.monitor_kind == LBM_MON_DRAG ? 1.0 / (0.5 * k.rho_out * k.monitor_u * k.monitor_u * k.monitor_l) : 0.0;
   const double nsamples = double((k.window_len - c->sample_from) / k.sample_every);
   if (k.lattice == LBM_D2Q9) {
     lbm::slice_end_kernel<<<k.nz, lbm::kEndThreads, 0, c->ls>>>(
-        c->at<double>(c->lay.partials), c->lay.igx, c->lay.igy, c->lay.fbs, c->lay.igx * c->lay.igy * c->lay.igz,
+        c->at<double>(c->lay.partials), c->lay.rgx, c->lay.iy, c->lay.rgx * c->lay.fy, c->lay.row_blocks,
         nsamples, c->at<double>(c->lay.slice_c), mon_scale, k.monitor_kind,
         c->at<double>(c->lay.slice_j));
     c->kernels += 1;
@@ -783,95 +768,6 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
     if (pipe) cudaEventRecord(c->adj_done[s & 1], main);
   }
   c->kernels_adjoint = c->kernels - k0;
-  return LBM_OK;
-}
-
-// The face table: for each face node (ascending index) its class, the mask of
-// unknowns completed by a rule, its inlet velocity, and per direction a the
-// node whose p_a becomes f_a (the upstream neighbour, or for a zero-gradient
-// outlet the neighbour's upstream node), the downstream node i + c_a, and the
-// zero-gradient node that copied p_a(i).
-template <class L>
-lbm_status build_face_table(lbm_ctx* c, const uint8_t* cls, const float* inlet_u) {
-  const lbm_config& k = c->cfg;
-  const Layout& lay = c->lay;
-  const unsigned nf = lay.nface;
-  if (nf == 0) return LBM_OK;
-  std::vector<float> uin(size_t(k.ny) * k.nz, 0.f);
-  if (inlet_u) {
-    CUDA_TRY(cudaMemcpy(uin.data(), inlet_u, uin.size() * 4, cudaMemcpyDefault));
-  }
-  std::vector<unsigned> idx, info, src(size_t(L::Q) * nf), dst(size_t(L::Q) * nf), ext(size_t(L::Q) * nf);
-  std::vector<float> u0;
-  idx.reserve(nf);
-  info.reserve(nf);
-  u0.reserve(nf);
-  const bool d3 = L::D == 3;
-  const int dims[3] = {k.nx, k.ny, k.nz};
-  auto nb = [&](int x, int y, int z, int dx, int dy, int dz, unsigned& j) {
-    int p[3] = {x + dx, y + dy, z + dz};
-    for (int a = 0; a < 3; ++a) {
-      if (p[a] < 0 || p[a] >= dims[a]) {
-        if (!k.periodic[a]) return false;
-        p[a] = (p[a] + dims[a]) % dims[a];
-      }
-    }
-    j = unsigned(p[0]) + unsigned(k.nx) * (unsigned(p[1]) + unsigned(k.ny) * unsigned(p[2]));
-    return true;
-  };
-  auto pad_to = [&](size_t rows) {   // empty rows (node kNone) up to a row count
-    while (idx.size() < rows) {
-      const unsigned r = unsigned(idx.size());
-      for (int a = 0; a < L::Q; ++a) src[size_t(a) * nf + r] = dst[size_t(a) * nf + r] = ext[size_t(a) * nf + r] = 0;
-      idx.push_back(lbm::kNone);
-      info.push_back(0);
-      u0.push_back(0.f);
-    }
-  };
-  for (int z = 0; z < k.nz; ++z) {
-    if (!d3) pad_to(size_t(z) * lay.fbs * lbm::kBlock);
-    for (int y = 0; y < k.ny; ++y)
-      for (int x = 0; x < k.nx; ++x) {
-        if (!(x == 0 || x == k.nx - 1 || y == 0 || y == k.ny - 1 || (d3 && (z == 0 || z == k.nz - 1)))) continue;
-        const unsigned i = unsigned(x) + unsigned(k.nx) * (unsigned(y) + unsigned(k.ny) * unsigned(z));
-        const unsigned r = unsigned(idx.size());
-        const uint8_t kind = cls[i];
-        unsigned mask = 0;
-        for (int a = 0; a < L::Q; ++a) {
-          unsigned j;
-          if (nb(x, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j)) {
-            src[size_t(a) * nf + r] = j;
-          } else if (kind == LBM_OUTLET_ZEROGRAD) {
-            const int xn = x == k.nx - 1 ? x - 1 : x + 1;
-            if (!nb(xn, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j)) return fail(LBM_ERR_ARG, "zero-gradient source outside");
-            src[size_t(a) * nf + r] = j;
-          } else {
-            src[size_t(a) * nf + r] = i;   // overwritten by the rule
-            mask |= 1u << a;
-          }
-          dst[size_t(a) * nf + r] = nb(x, y, z, L::cx(a), L::cy(a), L::cz(a), j) ? j : lbm::kNone;
-          unsigned e = lbm::kNone;
-          if ((x == k.nx - 1 && L::cx(a) == -1) || (x == 0 && L::cx(a) == 1)) {
-            if (nb(x, y, z, 0, L::cy(a), L::cz(a), j) && cls[j] == LBM_OUTLET_ZEROGRAD) e = j;
-          }
-          ext[size_t(a) * nf + r] = e;
-        }
-        if (kind == LBM_FLUID) mask = 0;
-        idx.push_back(i);
-        info.push_back(mask | (unsigned(kind) << 24));
-        u0.push_back(kind == LBM_INLET ? uin[size_t(y) + size_t(k.ny) * z] : 0.f);
-      }
-  }
-  if (!d3) pad_to(nf);
-  if (idx.size() != nf) return fail(LBM_ERR_ARG, "face count mismatch");
-  cudaStream_t s = c->stream;
-  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_idx), idx.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_info), info.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_u0), u0.data(), size_t(nf) * 4, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_src), src.data(), src.size() * 4, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_dst), dst.data(), dst.size() * 4, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(c->at(lay.f_ext), ext.data(), ext.size() * 4, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
   return LBM_OK;
 }
 
@@ -988,8 +884,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   CUDA_TRY(cudaMemsetAsync(x->at(lay.acc), 0, sizeof(lbm::WindowAcc), s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.flags), 0, 16, s));
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.cls), node_class, n, cudaMemcpyDefault, s));
-  if (c.lattice == LBM_D2Q9) LBM_TRY(build_face_table<D2Q9>(x, node_class, inlet_u));
-  else LBM_TRY(build_face_table<D3Q19>(x, node_class, inlet_u));
+  for (size_t k = 0; k < n && !x->has_zg; ++k) x->has_zg = node_class[k] == LBM_OUTLET_ZEROGRAD;
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.gamma), design_gamma, n * 4, cudaMemcpyDefault, s));
   if (objective_weights) CUDA_TRY(cudaMemcpyAsync(x->at(lay.wobj), objective_weights, n * 4, cudaMemcpyDefault, s));
   else CUDA_TRY(cudaMemsetAsync(x->at(lay.wobj), 0, n * 4, s));

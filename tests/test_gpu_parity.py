@@ -44,7 +44,8 @@ FWD_CASES = {
     # the layout of the U-bend workloads at reduced size: a velocity inlet and
     # a zero-gradient outlet side by side on the x = 0 face, walls and 3D wall
     # corners around them, the bend near x = nx-1
-    "ubend48x28x16": lambda: I.ubend_case(48, 28, 16, 8, tau=0.52, cs_smag=0.1, window_len=20, ckpt_every=20),
+    "ubend48x28x16": lambda: I.ubend_case(48, 28, 16, 8, tau=0.52, cs_smag=0.1, window_len=20, ckpt_every=20,
+                                          ckpt_format=I.CKPT_NATIVE),
 }
 
 

@@ -197,14 +197,23 @@ def kernel_hash():
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def measured_traffic(kernel, workload):
+def measured_traffic(kernel, case):
+    """DRAM bytes per launch of kernel on this workload from profiles/traffic.json:
+    an ncu capture of the workload itself, or of a smaller lattice of the same
+    family listed as scaling to it (bytes per node x this lattice's nodes;
+    DRAM traffic of a step grows with the node count).  None without a
+    capture of the current kernel source."""
     try:
         t = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
     for e in t.get("entries", []):
-        if e.get("kernel") == kernel and e.get("workload") == workload and e.get("source_hash") == kernel_hash():
+        if e.get("kernel") != kernel or e.get("source_hash") != kernel_hash():
+            continue
+        if e.get("workload") == case.name:
             return e.get("bytes_per_launch")
+        if case.name in e.get("scales_to", []):
+            return e["bytes_per_launch"] / e["nodes"] * case.n
     return None
 
 
@@ -244,22 +253,17 @@ def whole_job_mlups(lus_per_step_per_rank, steps, world, ms_max):
     return world * steps * lus_per_step_per_rank / (ms_max / 1e3) / 1e6
 
 
-def fwd_face_kernel(case):
-    """The forward face kernel the library launches for this lattice (face
-    positions from the geometry; the workloads have every extent >= 2)."""
-    return "fwd_face2d_kernel" if case.lattice == 9 else "fwd_face3d_kernel"
+FWD_KERNELS = ("fwd_row_kernel", "fwd_facerow_kernel")
+ADJ_KERNELS = ("adj_step_kernel",)
 
 
-def unit_traffic(unit, case, K):
-    """ncu DRAM bytes of one unit of work, from profiles/traffic.json (None if
-    any kernel involved has no capture for the current source)."""
-    fwd = [measured_traffic(k, case.name) for k in ("fwd_interior_kernel", fwd_face_kernel(case))]
-    adj = [measured_traffic(k, case.name) for k in ("adj_interior_kernel", "adj_face_kernel")]
-    if unit == "forward step":
-        return None if None in fwd else sum(fwd)
-    if None in fwd or None in adj:
-        return None
-    return sum(adj) + sum(fwd) * (K - 1) / K
+def unit_traffic(unit, case):
+    """ncu DRAM bytes of one launch of a step (forward: its two kernels;
+    adjoint: its kernel), None if a kernel has no capture for the current
+    source."""
+    ks = FWD_KERNELS if unit == "forward step" else ADJ_KERNELS
+    v = [measured_traffic(k, case) for k in ks]
+    return None if None in v else sum(v)
 
 
 def peaks():
@@ -564,32 +568,52 @@ def run_ours(args, case, rank, world, local):
     # and adjoint steps may run concurrently.
     sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / len(sweep_ev)
     sweep_b = (bytes_per_lu(case, "adjoint", rs=rs) + bytes_per_lu(case, "recompute", rs=rs) * (K - 1) / K) * n
-    fk = "fwd_interior_kernel+" + fwd_face_kernel(case)
-    ak = "adj_interior_kernel+adj_face_kernel"
-    units = {
-        "forward step": {"bytes": bytes_per_lu(case, "forward", rs=rs) * n,
-                         "us": phase_rows["forward"]["avg_step_us"], "kernel": fk,
-                         "total_ms": phase_rows["forward"]["ms"] / args.steps},
-        "adjoint sweep step": {"bytes": sweep_b, "us": 1e3 * sweep_ms / W,
-                               "kernel": f"{ak} with {fk} recompute", "total_ms": sweep_ms},
+    fk = "fwd_row_kernel+fwd_facerow_kernel"
+    ak = "adj_step_kernel"
+    # Kernels of a bench step: the forward-step pair (inner rows + face rows)
+    # runs W times in the window and S (K - 1) times in the recompute, the
+    # adjoint-step kernel W times.  Forward steps are timed in the window phase
+    # (nothing runs beside them); a serial sweep (--pipeline 0) times the
+    # recompute and adjoint phases apart, a pipelined one overlaps them, and
+    # then the adjoint step's time is the sweep step less its recompute share.
+    S = W // K
+    fwd_us = phase_rows["forward"]["avg_step_us"]
+    sweep_us = 1e3 * sweep_ms / W
+    serial = not args.pipeline
+    adj_us = phase_rows["adjoint"]["avg_step_us"] if serial else sweep_us - fwd_us * (K - 1) / K
+    kernels = {
+        "forward step": {"kernel": fk, "us": fwd_us, "launches": W + S * (K - 1),
+                         "bytes": bytes_per_lu(case, "forward", rs=rs) * n,
+                         "survey_bytes_per_lu": survey_bytes_per_lu(case, "forward step", rs=rs)},
+        "adjoint step": {"kernel": ak, "us": adj_us, "launches": W, "bytes": bytes_per_lu(case, "adjoint", rs=rs) * n,
+                         "survey_bytes_per_lu": (12 * case.lattice + 4 + 32) * rs // 4,
+                         "timing": "adjoint phase events (serial sweep)" if serial
+                                   else "sweep step less its recompute share (pipelined sweep)"},
     }
-    dom = max(units, key=lambda u: units[u]["total_ms"])
-    u = units[dom]
-    sv = survey_bytes_per_lu(case, dom, rs=rs) * n      # the scope table's count for the unit
+    for v in kernels.values():
+        v["ms_per_bench_step"] = v["us"] * v["launches"] / 1e3
+    dom = max(kernels, key=lambda k_: kernels[k_]["ms_per_bench_step"])
+    u = kernels[dom]
+    sv = u["survey_bytes_per_lu"] * n      # the scope table's count for one launch
     ach = sv / (u["us"] / 1e6) / 1e9
     ach_design = u["bytes"] / (u["us"] / 1e6) / 1e9
+    sweep_sv = survey_bytes_per_lu(case, "adjoint sweep step", rs=rs) * n
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": unit_traffic(dom, case, K),
-            "unit_of_work": dom, "kernel": u["kernel"], "bytes_per_unit": sv,
-            "bytes_per_lu": survey_bytes_per_lu(case, dom, rs=rs), "us_per_unit": u["us"],
-            "design_count": {"bytes_per_unit": u["bytes"], "bytes_per_lu": u["bytes"] / n,
-                             "achieved": ach_design, "frac": ach_design / hbm,
-                             "note": "this design's own algorithmic bytes (FP32 per-segment sensitivity partial, "
-                                     "no separate segment store); the headline uses the scope table's count"},
+            "traffic": unit_traffic(dom, case),
+            "dominant": dom, "kernel": u["kernel"], "bytes_per_launch": sv, "bytes_per_lu": u["survey_bytes_per_lu"],
+            "us_per_launch": u["us"], "launches_per_bench_step": u["launches"],
+            "design_count": {"bytes_per_launch": u["bytes"], "bytes_per_lu": u["bytes"] / n,
+                             "achieved": ach_design, "frac": ach_design / hbm},
             "peak_kind": f"{pk_kind} hbm_gbs (copy)",
             "timing": "CUDA events on the library stream inside the timed region: per forward-window phase, and "
                       "around each whole adjoint sweep",
-            "units": {k: {"us": v["us"], "gbs": v["bytes"] / (v["us"] / 1e6) / 1e9} for k, v in units.items()},
+            "kernels": {k_: {"us": v["us"], "launches": v["launches"], "ms_per_bench_step": v["ms_per_bench_step"],
+                             "gbs": v["survey_bytes_per_lu"] * n / (v["us"] / 1e6) / 1e9,
+                             "gbs_design_count": v["bytes"] / (v["us"] / 1e6) / 1e9} for k_, v in kernels.items()},
+            "adjoint_sweep_step": {"us": sweep_us, "survey_bytes_per_lu": survey_bytes_per_lu(case, "adjoint sweep step", rs=rs),
+                                   "gbs": sweep_sv / (sweep_us / 1e6) / 1e9, "frac": sweep_sv / (sweep_us / 1e6) / 1e9 / hbm,
+                                   "design_bytes_per_lu": sweep_b / n, "gbs_design_count": sweep_b / (sweep_us / 1e6) / 1e9,
+                                   "frac_design_count": sweep_b / (sweep_us / 1e6) / 1e9 / hbm},
             "phases": phase_rows}
 
     # Accuracy beside the number: the FP32 (or mixed-precision) window and

@@ -144,20 +144,88 @@ __device__ __forceinline__ int offset(const Geo& g, int a) {
 }
 
 // ---------------------------------------------------------------------------
-// Row geometry.  Each step runs two kernels on disjoint nodes, both over whole
-// lattice rows along x in blocks of kBlock threads starting at x = 0, so that
-// every warp's loads and stores cover whole, aligned 128-byte lines:
-//  * the row kernels take the inner rows (1 <= y <= ny-2 and, in 3D,
-//    1 <= z <= nz-2; every slice of a D2Q9 batch), x = 0 .. nx-1 included;
-//  * the face-row kernels take the rows on a y or z face, node by node from
-//    the geometry.
-// The x = 0 and x = nx-1 nodes of an inner row pull like every other node,
-// except that a link from outside the domain reads the node itself (an
-// in-row, don't-care value) and a periodic x axis wraps; the boundary rule
-// then replaces those links (xface_complete).  These functions are host and
-// device code so that the host can check every index a launch forms.
+// Row geometry.  The step kernels run over whole lattice rows along x, in
+// blocks of kBlock threads starting at x = 0, so that every warp's loads and
+// stores cover whole, aligned 128-byte lines.  The block that covers nodes
+// bx kBlock .. of row (y, z) keeps its sample partials in slot
+// bx + ceil(nx / kBlock) (y + ny z), whichever kernel runs it, so the rows of
+// one D2Q9 batch slice own consecutive slots.  Every node pulls with
+// branch-free index arithmetic: a link from outside the domain reads the node
+// itself (an in-row, don't-care value), a periodic axis wraps; the nodes with
+// such links (on a bounded face) then replace them by their boundary rule.
+// These functions are host and device code so that the host can check every
+// index a launch forms.
 // ---------------------------------------------------------------------------
 
+// Sample slot of the block covering nodes bx kBlock .. of row (y, z).
+HD unsigned row_slot(const Geo& g, int bx, int y, int z) {
+  return unsigned(bx) + unsigned((g.nx + kBlock - 1) / kBlock) * (unsigned(y) + unsigned(g.ny) * unsigned(z));
+}
+
+// Index the pull of direction a reads for node i at (x, y, z) (Eq. 7):
+// i - c_a with periodic wrap, or i itself for a link from outside the domain.
+template <class L>
+HD unsigned node_src(const Geo& g, int x, int y, int z, unsigned i, int a) {
+  unsigned j = i - unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
+  bool out = false;
+  if (L::cx(a) > 0 && x == 0) { if (g.px) j += unsigned(g.nx); else out = true; }
+  if (L::cx(a) < 0 && x == g.nx - 1) { if (g.px) j -= unsigned(g.nx); else out = true; }
+  if (L::cy(a) > 0 && y == 0) { if (g.py) j += g.sz; else out = true; }
+  if (L::cy(a) < 0 && y == g.ny - 1) { if (g.py) j -= g.sz; else out = true; }
+  if (L::cz(a) > 0 && z == 0) { if (g.pz) j += g.n; else out = true; }
+  if (L::cz(a) < 0 && z == g.nz - 1) { if (g.pz) j -= g.n; else out = true; }
+  return out ? i : j;
+}
+
+// Index the adjoint pull of direction a reads for node i (Eq. 36): i + c_a
+// with periodic wrap; kNone for a link that leaves the domain (adjoint 0).
+constexpr unsigned kNone = 0xffffffffu;
+template <class L>
+HD unsigned node_dst(const Geo& g, int x, int y, int z, unsigned i, int a) {
+  unsigned j = i + unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
+  bool out = false;
+  if (L::cx(a) < 0 && x == 0) { if (g.px) j += unsigned(g.nx); else out = true; }
+  if (L::cx(a) > 0 && x == g.nx - 1) { if (g.px) j -= unsigned(g.nx); else out = true; }
+  if (L::cy(a) < 0 && y == 0) { if (g.py) j += g.sz; else out = true; }
+  if (L::cy(a) > 0 && y == g.ny - 1) { if (g.py) j -= g.sz; else out = true; }
+  if (L::cz(a) < 0 && z == 0) { if (g.pz) j += g.n; else out = true; }
+  if (L::cz(a) > 0 && z == g.nz - 1) { if (g.pz) j -= g.n; else out = true; }
+  return out ? kNone : j;
+}
+
+// Links of node (x, y, z) that come from outside the domain (bounded axes).
+template <class L>
+HD unsigned node_unknowns(const Geo& g, int x, int y, int z) {
+  unsigned m = 0;
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) {
+    const bool out = (!g.px && ((L::cx(a) > 0 && x == 0) || (L::cx(a) < 0 && x == g.nx - 1))) ||
+                     (!g.py && ((L::cy(a) > 0 && y == 0) || (L::cy(a) < 0 && y == g.ny - 1))) ||
+                     (!g.pz && ((L::cz(a) > 0 && z == 0) || (L::cz(a) < 0 && z == g.nz - 1)));
+    if (out) m |= 1u << a;
+  }
+  return m;
+}
+
+// Node (x, y + dy, z + dz) on the same x plane (periodic wrap), or kNone
+// outside: where the adjoint looks for zero-gradient outlet nodes that
+// copied one of this node's populations.
+HD unsigned same_x_neighbour(const Geo& g, int y, int z, unsigned i, int dy, int dz) {
+  int Y = y + dy, Z = z + dz;
+  unsigned j = i + unsigned(dy * int(g.sy) + dz * int(g.sz));
+  if (Y < 0) { if (!g.py) return kNone; j += g.sz; }
+  if (Y >= g.ny) { if (!g.py) return kNone; j -= g.sz; }
+  if (Z < 0) { if (!g.pz) return kNone; j += g.n; }
+  if (Z >= g.nz) { if (!g.pz) return kNone; j -= g.n; }
+  return j;
+}
+
+// The forward step runs two kernels on disjoint rows: the inner rows
+// (1 <= y <= ny-2 and, in 3D, 1 <= z <= nz-2; every slice of a D2Q9 batch),
+// whose only links from outside the domain are those of the x = 0 and
+// x = nx-1 nodes on a bounded x axis, and the face rows (on a y or z face).
+// The inner-row kernel keeps the x-face completion to those links, which
+// keeps its registers, and so its occupancy, at those of a plain pull.
 // Inner rows per z (D3Q19: z interior; D2Q9: every slice) and z of inner row block rz.
 template <class L>
 HD int inner_rows_y(const Geo& g) { return g.ny > 2 ? g.ny - 2 : 0; }
@@ -194,17 +262,6 @@ HD unsigned row_src(const Geo& g, int x, unsigned i, int a) {
   unsigned j = i - unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
   if (L::cx(a) > 0 && x == 0) j = g.px ? j + unsigned(g.nx) : i;
   if (L::cx(a) < 0 && x == g.nx - 1) j = g.px ? j - unsigned(g.nx) : i;
-  return j;
-}
-
-// Index the adjoint pull of direction a reads for inner-row node i at x
-// (Eq. 36): i + c_a; kNone for a link that leaves the domain (its adjoint is 0).
-constexpr unsigned kNone = 0xffffffffu;
-template <class L>
-HD unsigned row_dst(const Geo& g, int x, unsigned i, int a) {
-  unsigned j = i + unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
-  if (L::cx(a) < 0 && x == 0) j = g.px ? j + unsigned(g.nx) : kNone;
-  if (L::cx(a) > 0 && x == g.nx - 1) j = g.px ? j - unsigned(g.nx) : kNone;
   return j;
 }
 
@@ -653,6 +710,36 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
   }
 }
 
+// Pull of node i (Eq. 7) with its boundary completion (Eqs. 19-21, the 3D
+// velocity inlet): the links from outside the domain take the node's rule,
+// or for a zero-gradient outlet the post-streaming value of the neighbour
+// along the inward normal, p_a(i + n_in - c_a).  Returns the links completed
+// by a rule (0 off the bounded faces and for a zero-gradient outlet, whose
+// links are copies), with the node's class and inlet velocity.
+template <class L, class R>
+__device__ __forceinline__ unsigned node_gather(const R* __restrict__ P, const uint8_t* __restrict__ cls_arr,
+                                                const float* __restrict__ uin, R rho_out, const Geo& g, int x, int y,
+                                                int z, unsigned i, R (&f)[L::Q], uint8_t& cls, R& u0) {
+#pragma unroll
+  for (int a = 0; a < L::Q; ++a) f[a] = P[a * g.n + node_src<L>(g, x, y, z, i, a)];
+  cls = FLUID;
+  u0 = R(0);
+  const unsigned mask = node_unknowns<L>(g, x, y, z);
+  if (!mask) return 0u;
+  cls = cls_arr[i];
+  if (cls == INLET) u0 = R(uin[unsigned(y) + unsigned(g.ny) * unsigned(z)]);
+  if (cls == OUTLET_ZG) {
+    const int xn = x == 0 ? 1 : x - 1;
+    const unsigned k = x == 0 ? i + 1u : i - 1u;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a)
+      if (mask & (1u << a)) f[a] = P[a * g.n + node_src<L>(g, xn, y, z, k, a)];
+    return 0u;
+  }
+  apply_rules<L, R>(f, mask, cls, u0, rho_out);
+  return mask;
+}
+
 // Completion of an x-face node of an inner row (bounded x axis): the links in
 // mask came from outside the domain and take the node's rule (Eqs. 19-21, the
 // 3D velocity inlet), or for a zero-gradient outlet the post-streaming value
@@ -708,7 +795,7 @@ __global__ void __launch_bounds__(kBlock) fwd_row_kernel(FwdArgs<R> A) {
   }
   if (A.sample) {   // uniform across the grid
     block_sum2<R>(bj, bm);
-    ring_store(bj, bm, A.ring, size_t(A.sample - 1) * A.nblk + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+    ring_store(bj, bm, A.ring, size_t(A.sample - 1) * A.nblk + row_slot(g, int(blockIdx.x), y, z));
   }
 }
 
@@ -727,9 +814,9 @@ __device__ __forceinline__ void face_geo_node(const FwdArgs<R>& A, int x, int y,
 }
 
 // Forward step over the face rows: one block row of the grid per face row
-// (face_row_yz); block sums after the row kernel's (blk0 onward).
+// (face_row_yz).
 template <class L, class R, bool MOM = false>
-__global__ void __launch_bounds__(kBlock) fwd_facerow_kernel(FwdArgs<R> A, unsigned blk0) {
+__global__ void __launch_bounds__(kBlock) fwd_facerow_kernel(FwdArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
   const int x = int(blockIdx.x) * kBlock + int(threadIdx.x);
@@ -739,7 +826,7 @@ __global__ void __launch_bounds__(kBlock) fwd_facerow_kernel(FwdArgs<R> A, unsig
   if (x < g.nx) face_geo_node<L, R, MOM>(A, x, y, z, bj, bm);
   if (A.sample) {
     block_sum2<R>(bj, bm);
-    ring_store(bj, bm, A.ring, size_t(A.sample - 1) * A.nblk + blk0 + blockIdx.x + gridDim.x * blockIdx.y);
+    ring_store(bj, bm, A.ring, size_t(A.sample - 1) * A.nblk + row_slot(g, int(blockIdx.x), y, z));
   }
 }
 
@@ -793,20 +880,17 @@ __global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, in
 }
 
 // Per-slice window means of a batch of independent 2D lattices (D2Q9, nz > 1):
-// one block per slice sums the block sums of that slice's interior blocks
-// (bz == slice) and face blocks (slice-aligned) in a fixed order.  Runs
-// before window_end_kernel, which clears the block sums.
-__global__ void __launch_bounds__(kEndThreads) slice_end_kernel(const double* blk, int igx, int igy, int fbs,
-                                                                int nint, double nsamples, const double* jconst,
-                                                                double mon_scale, int mon_kind, double* out) {
+// one block per slice sums the block sums of that slice's rows (per_slice
+// consecutive blocks of the step grid) in a fixed order.  Runs before
+// window_end_kernel, which clears the block sums.
+__global__ void __launch_bounds__(kEndThreads) slice_end_kernel(const double* blk, int per_slice, double nsamples,
+                                                                const double* jconst, double mon_scale, int mon_kind,
+                                                                double* out) {
   __shared__ double sh[4][kEndThreads];
   const int slice = blockIdx.x, t = threadIdx.x;
-  const int nib = igx * igy;              // interior blocks of one slice
-  const int count = nib + fbs;
   double sj = 0, cj = 0, sm = 0, cm = 0;
-  for (int b = t; b < count; b += kEndThreads) {
-    const int bid = b < nib ? slice * nib + b : nint + slice * fbs + (b - nib);
-    const Sums a = reinterpret_cast<const Sums*>(blk)[bid];
+  for (int b = t; b < per_slice; b += kEndThreads) {
+    const Sums a = reinterpret_cast<const Sums*>(blk)[size_t(slice) * per_slice + b];
     neumaier(sj, cj, a.x);
     neumaier(sj, cj, a.y);
     neumaier(sm, cm, a.z);
@@ -964,11 +1048,11 @@ struct AdjStep {
   int terminal;
 };
 
-// One node of an adjoint step.  ROW: a node of an inner row (row geometry:
-// the adjoint pull of Eq. 36 by row_dst, the x-face completion and its
-// transpose on the first and last node of a row); otherwise a face-row node
-// with every index from the geometry (pull_face, gather_geo).
-template <class L, class R, bool ROW>
+// One node of an adjoint step (row geometry): the adjoint pull of Eq. 36
+// (node_dst) plus the transposed zero-gradient copies, the transposed
+// collision and blend (Eqs. 30-35) and the transposed boundary rule
+// (Eqs. 37-39).
+template <class L, class R>
 __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<R>& P, int x, int y, int z, unsigned i) {
   const Geo& g = A.geo;
   const R* bnext = P.bnext;
@@ -983,25 +1067,23 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
     if (P.terminal) {
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) a[k] = R(0);
-    } else if (ROW) {
+    } else {
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) {
-        const unsigned j = row_dst<L>(g, x, i, k);
+        const unsigned j = node_dst<L>(g, x, y, z, i, k);
         a[k] = j != kNone ? bnext[k * g.n + j] : R(0);
       }
       // A zero-gradient outlet node j on this x face copied p_k(i) into its
       // unknown f_k(j), j = i + c_k - n_in: pull those adjoints back.
-      if (A.zg && row_unknowns<L>(g, x)) {
+      if (A.zg && !g.px && (x == 0 || x == g.nx - 1)) {
         const int sx = x == 0 ? 1 : -1;
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
           if (L::cx(k) != sx) continue;
-          const unsigned j = i + unsigned(L::cy(k) * int(g.sy) + L::cz(k) * int(g.sz));
-          if (A.cls[j] == OUTLET_ZG) a[k] += bnext[k * g.n + j];
+          const unsigned j = same_x_neighbour(g, y, z, i, L::cy(k), L::cz(k));
+          if (j != kNone && A.cls[j] == OUTLET_ZG) a[k] += bnext[k * g.n + j];
         }
       }
-    } else {
-      pull_face<L, R>(bnext, A.cls, g, x, y, z, a);
     }
     raw_moments<L, R, true>(a, A0, A1, A2);
   }
@@ -1009,15 +1091,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
   R f[L::Q];
   uint8_t cls;
   R u0;
-  unsigned mask;
-  if (ROW) {
-    mask = row_gather<L, R>(pprev, A.cls, A.uin, A.ph.rho_out, g, x, y, z, i, f, cls, u0);
-  } else {
-    cls = A.cls[i];
-    u0 = cls == INLET ? R(A.uin[unsigned(y) + unsigned(g.ny) * unsigned(z)]) : R(0);
-    const unsigned unk = gather_geo<L, R>(pprev, g, x, y, z, cls, u0, A.ph.rho_out, f);
-    mask = (cls == FLUID || cls == OUTLET_ZG) ? 0u : unk;
-  }
+  const unsigned mask = node_gather<L, R>(pprev, A.cls, A.uin, A.ph.rho_out, g, x, y, z, i, f, cls, u0);
   Mom<L, R> M;
   moments<L, R>(f, A.ph, M);
   const R gi = A.gfield[i];
@@ -1125,29 +1199,17 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
   if (x >= d[0] && x < d[1] && y >= d[2] && y < d[3] && z >= d[4] && z < d[5]) A.gpart[i] += gt;
 }
 
-// Adjoint step over the inner rows and over the face rows (the row geometry
-// of the forward step).
+// One adjoint step over every node: grid (ceil(nx / kBlock), ny, nz).  Unlike
+// the forward step it needs no split into inner and face rows: its boundary
+// completion costs no occupancy (measured: one kernel beats the pair).
 template <class L, class R>
-__global__ void __launch_bounds__(kBlock) adj_row_kernel(AdjArgs<R> A) {
+__global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
-  const int x = int(blockIdx.x) * kBlock + int(threadIdx.x), y = 1 + int(blockIdx.y);
-  const int z = L::D == 3 ? 1 + int(blockIdx.z) : int(blockIdx.z);   // D2Q9: z is the slice of a batch
+  const int x = int(blockIdx.x) * kBlock + int(threadIdx.x), y = int(blockIdx.y), z = int(blockIdx.z);
   if (x >= g.nx) return;
-  adjoint_node<L, R, true>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z,
-                           unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz);
-}
-
-template <class L, class R>
-__global__ void __launch_bounds__(kBlock) adj_facerow_kernel(AdjArgs<R> A) {
-  pdl_enter();
-  const Geo& g = A.geo;
-  const int x = int(blockIdx.x) * kBlock + int(threadIdx.x);
-  if (x >= g.nx) return;
-  int y, z;
-  face_row_yz<L>(g, int(blockIdx.y), y, z);
-  adjoint_node<L, R, false>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z,
-                            unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz);
+  adjoint_node<L, R>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z,
+                     unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz);
 }
 
 // Fold a segment's sensitivity partials into the FP64 (sum, compensation)

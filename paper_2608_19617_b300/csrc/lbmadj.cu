@@ -85,10 +85,8 @@ struct Layout {
       total;
   int nblocks_fwd, nblocks_1d, nslots;
   int rgx;                    // blocks of kBlock along a row (x = 0 .. nx-1)
-  int iy, iz;                 // inner rows along y and z (row kernels' grid)
-  int nfr;                    // face rows (face-row kernels' grid)
-  int fy;                     // face rows per z (D2Q9: per slice)
-  int row_blocks;             // row-kernel blocks; face-row blocks follow in the block sums
+  int iy, iz;                 // inner rows along y and z (forward row kernel's grid)
+  int nfr;                    // face rows (forward face-row kernel's grid)
   size_t seg_sets;            // 2 when recompute and adjoint are pipelined
   bool stage_in_seg;
 };
@@ -138,17 +136,15 @@ Layout make_layout(const lbm_config& c) {
   const int d = c.lattice == LBM_D2Q9 ? 2 : 3;
   const size_t rs = c.precision == LBM_FP64 ? 8 : 4;
   const size_t lat = align_up(size_t(q) * n * rs);
-  // Inner rows run in the row kernels, the rows of the y and z faces in the
-  // face-row kernels (kernels.cuh, row geometry); both cover whole rows.
+  // Whole rows along x (kernels.cuh, row geometry): the forward step runs the
+  // inner rows and the face rows in two kernels, the adjoint step all rows in
+  // one; one sample slot per block of a row.
   const bool d2 = c.lattice == LBM_D2Q9;
   L.rgx = (c.nx + lbm::kBlock - 1) / lbm::kBlock;
   L.iy = c.ny > 2 ? c.ny - 2 : 0;
   L.iz = d2 ? c.nz : (c.nz > 2 ? c.nz - 2 : 0);
-  L.fy = c.ny >= 2 ? 2 : 1;
-  const int fz = c.nz >= 2 ? 2 : 1;
-  L.nfr = L.fy * c.nz + (d2 ? 0 : fz * L.iy);
-  L.row_blocks = L.rgx * L.iy * L.iz;
-  L.nblocks_fwd = L.row_blocks + L.rgx * L.nfr;
+  L.nfr = (c.ny >= 2 ? 2 : 1) * c.nz + (d2 ? 0 : (c.nz >= 2 ? 2 : 1) * L.iy);
+  L.nblocks_fwd = L.rgx * c.ny * c.nz;
   L.nblocks_1d = int((n + lbm::kBlock - 1) / lbm::kBlock);
   L.nslots = c.window_len / c.ckpt_every;
   const bool native = c.ckpt_format == LBM_CKPT_NATIVE;
@@ -235,7 +231,7 @@ struct lbm_ctx {
   cudaStream_t stream;        // the caller's stream: everything runs in its order
   cudaStream_t ls = nullptr;  // stream launches go to (the capture stream while capturing)
   cudaStream_t cap = nullptr; // private stream used only to capture graphs
-  cudaStream_t side = nullptr;            // face kernels run here, forked from ls and joined back
+  cudaStream_t side = nullptr;            // forward face-row kernels run here, forked from ls and joined back
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // Pipelined adjoint: the recompute of the next segment runs on rec (with its
   // own side stream) while the adjoint of the current segment runs on ls.
@@ -355,8 +351,8 @@ struct lbm_ctx {
     for (auto& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
     for (auto e : pool) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
-    if (side) cudaStreamDestroy(side);
     if (rec) cudaStreamDestroy(rec);
+    if (side) cudaStreamDestroy(side);
     if (rec_side) cudaStreamDestroy(rec_side);
     for (cudaEvent_t e : {fork_ev, join_ev, rec_fork, rec_join, start_ev, rec_done[0], rec_done[1], adj_done[0], adj_done[1]})
       if (e) cudaEventDestroy(e);
@@ -375,9 +371,25 @@ struct ImplT final : Impl {
     long long b = (long long)(c->n * c->q + 255) / 256;
     return int(b < 148 * 32 ? b : 148 * 32);
   }
+  dim3 sgrid() const { return dim3(c->lay.rgx, c->cfg.ny, c->cfg.nz); }
   dim3 rgrid() const { return dim3(c->lay.rgx, c->lay.iy, c->lay.iz); }
   dim3 fgrid() const { return dim3(c->lay.rgx, c->lay.nfr); }
-  bool has_interior() const { return c->lay.row_blocks > 0; }
+  // Inner-row kernel on the launch stream, face-row kernel on the side
+  // stream, forked and joined with events so that both run concurrently (and
+  // become parallel branches when captured into a graph).
+  template <class IK, class FK>
+  void fork_join(IK inner, FK face) {
+    cudaEventRecord(c->fork_cur, c->ls);
+    cudaStreamWaitEvent(c->side_cur, c->fork_cur, 0);
+    face(c->side_cur);
+    c->kernels += 1;
+    if (c->lay.iy > 0 && c->lay.iz > 0) {
+      inner(c->ls);
+      c->kernels += 1;
+    }
+    cudaEventRecord(c->join_cur, c->side_cur);
+    cudaStreamWaitEvent(c->ls, c->join_cur, 0);
+  }
   // Step kernels: optionally with programmatic stream serialization, so that a
   // launch overlaps the tail of its predecessor (the kernel waits in
   // pdl_enter before touching data).
@@ -401,22 +413,6 @@ struct ImplT final : Impl {
     } else {
       kernel<<<grid, block, 0, st>>>(args...);
     }
-  }
-  // Interior kernel on the launch stream, face kernel on the side stream,
-  // forked and joined with events so that both run concurrently (and become
-  // parallel branches when captured into a graph).
-  template <class IK, class FK>
-  void fork_join(IK interior, FK face) {
-    cudaEventRecord(c->fork_cur, c->ls);
-    cudaStreamWaitEvent(c->side_cur, c->fork_cur, 0);
-    face(c->side_cur);
-    c->kernels += 1;
-    if (has_interior()) {
-      interior(c->ls);
-      c->kernels += 1;
-    }
-    cudaEventRecord(c->join_cur, c->side_cur);
-    cudaStreamWaitEvent(c->ls, c->join_cur, 0);
   }
   lbm::Phys<R> phys() const { return {R(c->cfg.tau), R(c->cfg.cs_smag * c->cfg.cs_smag), R(c->cfg.rho_out)}; }
   lbm::Obj<R> obj() const {
@@ -468,25 +464,25 @@ struct ImplT final : Impl {
     A.zg = c->has_zg ? 1 : 0;
     return A;
   }
+  // One forward step: the inner rows and the face rows concurrently (a
+  // moment-checkpoint step runs its own instantiation, MOM).
   void fwd(const void* src, void* dst, int sample, void* mom) override {
     const lbm::FwdArgs<R> A = fwd_args(src, dst, sample, mom);
-    const unsigned blk0 = unsigned(c->lay.row_blocks);
-    // the step that writes a moment checkpoint runs its own instantiation (MOM)
     fork_join(
         [&](cudaStream_t st) {
           if (mom) launch(lbm::fwd_row_kernel<L, R, true>, rgrid(), st, A);
           else launch(lbm::fwd_row_kernel<L, R, false>, rgrid(), st, A);
         },
         [&](cudaStream_t st) {
-          if (mom) launch(lbm::fwd_facerow_kernel<L, R, true>, fgrid(), st, A, blk0);
-          else launch(lbm::fwd_facerow_kernel<L, R, false>, fgrid(), st, A, blk0);
+          if (mom) launch(lbm::fwd_facerow_kernel<L, R, true>, fgrid(), st, A);
+          else launch(lbm::fwd_facerow_kernel<L, R, false>, fgrid(), st, A);
         });
   }
 
   void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
     const lbm::AdjArgs<R> A = adj_args(bnext, pprev, bout, sample);
-    fork_join([&](cudaStream_t st) { launch(lbm::adj_row_kernel<L, R>, rgrid(), st, A); },
-              [&](cudaStream_t st) { launch(lbm::adj_facerow_kernel<L, R>, fgrid(), st, A); });
+    launch(lbm::adj_step_kernel<L, R>, sgrid(), c->ls, A);
+    c->kernels += 1;
   }
 
   const void* checkpoint_field(int s) override {
@@ -688,7 +684,7 @@ lbm_status enqueue_window(lbm_ctx* c) {
   const double nsamples = double((k.window_len - c->sample_from) / k.sample_every);
   if (k.lattice == LBM_D2Q9) {
     lbm::slice_end_kernel<<<k.nz, lbm::kEndThreads, 0, c->ls>>>(
-        c->at<double>(c->lay.partials), c->lay.rgx, c->lay.iy, c->lay.rgx * c->lay.fy, c->lay.row_blocks,
+        c->at<double>(c->lay.partials), c->lay.rgx * k.ny,
         nsamples, c->at<double>(c->lay.slice_c), mon_scale, k.monitor_kind,
         c->at<double>(c->lay.slice_j));
     c->kernels += 1;
@@ -717,7 +713,7 @@ lbm_status enqueue_adjoint(lbm_ctx* c) {
   CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gacc), 0, c->n * 16, c->ls));
   CUDA_TRY(cudaMemsetAsync(c->at(c->lay.gpart), 0, c->n * c->rs, c->ls));
   cudaStream_t main = c->ls;
-  auto on_rec = [&](bool rec) {   // route launches (and their face kernels) to one pipeline stream
+  auto on_rec = [&](bool rec) {   // route launches (and their face-row kernels) to one pipeline stream
     c->ls = rec ? c->rec : main;
     c->side_cur = rec ? c->rec_side : c->side;
     c->fork_cur = rec ? c->rec_fork : c->fork_ev;

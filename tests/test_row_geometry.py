@@ -1,8 +1,8 @@
 """Host check of the step kernels' index arithmetic: row_geometry_check.cu
 includes the kernels' own host-and-device row geometry and enumerates every
-thread of every row and face-row launch on many lattice shapes (periodic and
-bounded axes, D2Q9 batches), checking coverage, every population index read
-and every block-sum slot.  Runs on the CPU (nvcc builds a host program)."""
+thread of the step launches on many lattice shapes (periodic and bounded
+axes, D2Q9 batches), checking coverage, the unknown links, every population
+index read and every block-sum slot.  Runs on the CPU (nvcc builds a host program)."""
 import os
 import shutil
 import subprocess

@@ -108,8 +108,9 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
   s = t;
 }
 
-// Neighbour (x+dx, y+dy, z+dz) with periodic wrap; false if outside.
-__device__ __forceinline__ bool neighbour(const Geo& g, int x, int y, int z, int dx, int dy, int dz,
+// Neighbour (x+dx, y+dy, z+dz) with periodic wrap; false if outside.  Host
+// and device code, so that the host can check the face gathers' indices.
+HD bool neighbour(const Geo& g, int x, int y, int z, int dx, int dy, int dz,
                                           unsigned& j) {
   int X = x + dx, Y = y + dy, Z = z + dz;
   if (X < 0 || X >= g.nx) { if (!g.px) return false; X = (X + g.nx) % g.nx; }

@@ -86,6 +86,25 @@ static void check(int nx, int ny, int nz, int px, int py, int pz) {
               CHECK(want >= 0 && (long long)zg == want, "zero-gradient source of a=%d at (%d,%d,%d)", a, x, y, z);
             }
           }
+          // the face gathers (gather_geo, pull_face): neighbour() for every link,
+          // and the zero-gradient copy's upstream node where such an outlet may sit
+          for (int a = 0; a < L::Q; ++a) {
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+              unsigned j = 0;
+              const bool in = neighbour(g, x, y, z, sgn * L::cx(a), sgn * L::cy(a), sgn * L::cz(a), j);
+              const long long want = nb(g, x, y, z, sgn * L::cx(a), sgn * L::cy(a), sgn * L::cz(a));
+              CHECK(in == (want >= 0) && (!in || (long long)j == want), "neighbour of a=%d at (%d,%d,%d)", a, x, y, z);
+            }
+          }
+          if (left || (right && mask == xface1)) {
+            const int xn = x == 0 ? 1 : x - 1;
+            for (int a = 0; a < L::Q; ++a) {
+              if (!((mask >> a) & 1u)) continue;
+              unsigned j = 0;
+              const bool in = neighbour(g, xn, y, z, -L::cx(a), -L::cy(a), -L::cz(a), j);
+              CHECK(in && (long long)j < n, "gather_geo zero-gradient source of a=%d at (%d,%d,%d)", a, x, y, z);
+            }
+          }
           if (!px && (x == 0 || x == nx - 1)) {   // the adjoint's same-face neighbours
             for (int k = 0; k < L::Q; ++k) {
               const unsigned j = same_x_neighbour(g, y, z, i, L::cy(k), L::cz(k));

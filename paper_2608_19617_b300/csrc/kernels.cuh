@@ -566,9 +566,12 @@ __device__ __forceinline__ void sample_commit(double bj, double bm, double* blk)
 // The per-step kernels leave each sampled step's block partials (j, monitor)
 // in the working precision in a ring of slots, one store by thread 0 and no
 // read, so a block's last warp retires as soon as its reduction is done.
-// sample_fold_kernel then adds the slots into the blocks' FP64 (sum,
-// compensation) window sums, slot by slot in step order: the same additions,
-// in the same order, as adding each step's partial right away.
+// sample_fold_kernel then adds them into the blocks' FP64 (sum, compensation)
+// window sums: one thread per block and quantity sums its slots in step order
+// in FP64 (each partial converts exactly; 32 additions round at 2^-53
+// relative) and adds that into the pair with one Neumaier step.  FP64
+// arithmetic is scarce on B300 (about 1/64 of the FP32 rate), so the fold
+// keeps it to one addition per slot.
 template <class R>
 __device__ __forceinline__ void ring_store(R bj, R bm, R* ring, size_t slot) {
   if (threadIdx.x == 0) {
@@ -579,14 +582,12 @@ __device__ __forceinline__ void ring_store(R bj, R bm, R* ring, size_t slot) {
 
 template <class R>
 __global__ void sample_fold_kernel(const R* __restrict__ ring, int count, unsigned nblk, double* __restrict__ blk) {
-  for (unsigned b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
-    Sums a = reinterpret_cast<Sums*>(blk)[b];
-    for (int r = 0; r < count; ++r) {
-      const size_t k = 2 * (size_t(r) * nblk + b);
-      neumaier(a.x, a.y, double(ring[k]));
-      neumaier(a.z, a.w, double(ring[k + 1]));
-    }
-    reinterpret_cast<Sums*>(blk)[b] = a;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < 2u * nblk; t += gridDim.x * blockDim.x) {
+    // t = 2 b + q: block b, quantity q (0: objective, 1: monitor); ring[2 (r nblk + b) + q]
+    double s = 0.0;
+    for (int r = 0; r < count; ++r) s += double(ring[2 * size_t(r) * nblk + t]);
+    double* pair = blk + 2 * size_t(t);   // Sums: (j sum, j comp, monitor sum, monitor comp)
+    neumaier(pair[0], pair[1], s);
   }
 }
 
@@ -834,7 +835,7 @@ __global__ void __launch_bounds__(kBlock) fwd_facerow_kernel(FwdArgs<R> A) {
 // Window end (one block of kEndThreads): sum the per-block window sums in a
 // fixed order with compensation, form the means of Eq. 42 and the ratio of
 // Eq. 26, and clear the block sums for the next window.
-constexpr int kEndThreads = 256;
+constexpr int kEndThreads = 1024;
 __global__ void __launch_bounds__(kEndThreads) window_end_kernel(double* blk, int nblocks, WindowAcc* acc,
                                                                  double tol, const int* nonfinite,
                                                                  double nsamples, double jconst,

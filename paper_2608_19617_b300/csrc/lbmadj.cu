@@ -503,7 +503,7 @@ struct ImplT final : Impl {
   }
 
   void fold(int count) override {
-    const int nb = int(std::min<long long>((c->lay.nblocks_fwd + 255) / 256, 148 * 8));
+    const int nb = int(std::min<long long>((2LL * c->lay.nblocks_fwd + 255) / 256, 148 * 8));
     c->kernels += 1;
     lbm::sample_fold_kernel<R><<<nb, 256, 0, c->ls>>>(c->template at<R>(c->lay.ring), count,
                                                       unsigned(c->lay.nblocks_fwd), c->template at<double>(c->lay.partials));

@@ -165,44 +165,45 @@ HD unsigned row_slot(const Geo& g, int bx, int y, int z) {
 
 // Index the pull of direction a reads for node i at (x, y, z) (Eq. 7):
 // i - c_a with periodic wrap, or i itself for a link from outside the domain.
-template <class L>
+// PER = false: the lattice has no periodic axis (the wrap arithmetic compiles out).
+template <class L, bool PER = true>
 HD unsigned node_src(const Geo& g, int x, int y, int z, unsigned i, int a) {
   unsigned j = i - unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
   bool out = false;
-  if (L::cx(a) > 0 && x == 0) { if (g.px) j += unsigned(g.nx); else out = true; }
-  if (L::cx(a) < 0 && x == g.nx - 1) { if (g.px) j -= unsigned(g.nx); else out = true; }
-  if (L::cy(a) > 0 && y == 0) { if (g.py) j += g.sz; else out = true; }
-  if (L::cy(a) < 0 && y == g.ny - 1) { if (g.py) j -= g.sz; else out = true; }
-  if (L::cz(a) > 0 && z == 0) { if (g.pz) j += g.n; else out = true; }
-  if (L::cz(a) < 0 && z == g.nz - 1) { if (g.pz) j -= g.n; else out = true; }
+  if (L::cx(a) > 0 && x == 0) { if (PER && g.px) j += unsigned(g.nx); else out = true; }
+  if (L::cx(a) < 0 && x == g.nx - 1) { if (PER && g.px) j -= unsigned(g.nx); else out = true; }
+  if (L::cy(a) > 0 && y == 0) { if (PER && g.py) j += g.sz; else out = true; }
+  if (L::cy(a) < 0 && y == g.ny - 1) { if (PER && g.py) j -= g.sz; else out = true; }
+  if (L::cz(a) > 0 && z == 0) { if (PER && g.pz) j += g.n; else out = true; }
+  if (L::cz(a) < 0 && z == g.nz - 1) { if (PER && g.pz) j -= g.n; else out = true; }
   return out ? i : j;
 }
 
 // Index the adjoint pull of direction a reads for node i (Eq. 36): i + c_a
 // with periodic wrap; kNone for a link that leaves the domain (adjoint 0).
 constexpr unsigned kNone = 0xffffffffu;
-template <class L>
+template <class L, bool PER = true>
 HD unsigned node_dst(const Geo& g, int x, int y, int z, unsigned i, int a) {
   unsigned j = i + unsigned(L::cx(a) + L::cy(a) * int(g.sy) + L::cz(a) * int(g.sz));
   bool out = false;
-  if (L::cx(a) < 0 && x == 0) { if (g.px) j += unsigned(g.nx); else out = true; }
-  if (L::cx(a) > 0 && x == g.nx - 1) { if (g.px) j -= unsigned(g.nx); else out = true; }
-  if (L::cy(a) < 0 && y == 0) { if (g.py) j += g.sz; else out = true; }
-  if (L::cy(a) > 0 && y == g.ny - 1) { if (g.py) j -= g.sz; else out = true; }
-  if (L::cz(a) < 0 && z == 0) { if (g.pz) j += g.n; else out = true; }
-  if (L::cz(a) > 0 && z == g.nz - 1) { if (g.pz) j -= g.n; else out = true; }
+  if (L::cx(a) < 0 && x == 0) { if (PER && g.px) j += unsigned(g.nx); else out = true; }
+  if (L::cx(a) > 0 && x == g.nx - 1) { if (PER && g.px) j -= unsigned(g.nx); else out = true; }
+  if (L::cy(a) < 0 && y == 0) { if (PER && g.py) j += g.sz; else out = true; }
+  if (L::cy(a) > 0 && y == g.ny - 1) { if (PER && g.py) j -= g.sz; else out = true; }
+  if (L::cz(a) < 0 && z == 0) { if (PER && g.pz) j += g.n; else out = true; }
+  if (L::cz(a) > 0 && z == g.nz - 1) { if (PER && g.pz) j -= g.n; else out = true; }
   return out ? kNone : j;
 }
 
 // Links of node (x, y, z) that come from outside the domain (bounded axes).
-template <class L>
+template <class L, bool PER = true>
 HD unsigned node_unknowns(const Geo& g, int x, int y, int z) {
   unsigned m = 0;
 #pragma unroll
   for (int a = 0; a < L::Q; ++a) {
-    const bool out = (!g.px && ((L::cx(a) > 0 && x == 0) || (L::cx(a) < 0 && x == g.nx - 1))) ||
-                     (!g.py && ((L::cy(a) > 0 && y == 0) || (L::cy(a) < 0 && y == g.ny - 1))) ||
-                     (!g.pz && ((L::cz(a) > 0 && z == 0) || (L::cz(a) < 0 && z == g.nz - 1)));
+    const bool out = (!(PER && g.px) && ((L::cx(a) > 0 && x == 0) || (L::cx(a) < 0 && x == g.nx - 1))) ||
+                     (!(PER && g.py) && ((L::cy(a) > 0 && y == 0) || (L::cy(a) < 0 && y == g.ny - 1))) ||
+                     (!(PER && g.pz) && ((L::cz(a) > 0 && z == 0) || (L::cz(a) < 0 && z == g.nz - 1)));
     if (out) m |= 1u << a;
   }
   return m;
@@ -718,15 +719,15 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
 // along the inward normal, p_a(i + n_in - c_a).  Returns the links completed
 // by a rule (0 off the bounded faces and for a zero-gradient outlet, whose
 // links are copies), with the node's class and inlet velocity.
-template <class L, class R>
+template <class L, class R, bool PER = true>
 __device__ __forceinline__ unsigned node_gather(const R* __restrict__ P, const uint8_t* __restrict__ cls_arr,
                                                 const float* __restrict__ uin, R rho_out, const Geo& g, int x, int y,
                                                 int z, unsigned i, R (&f)[L::Q], uint8_t& cls, R& u0) {
 #pragma unroll
-  for (int a = 0; a < L::Q; ++a) f[a] = P[a * g.n + node_src<L>(g, x, y, z, i, a)];
+  for (int a = 0; a < L::Q; ++a) f[a] = P[a * g.n + node_src<L, PER>(g, x, y, z, i, a)];
   cls = FLUID;
   u0 = R(0);
-  const unsigned mask = node_unknowns<L>(g, x, y, z);
+  const unsigned mask = node_unknowns<L, PER>(g, x, y, z);
   if (!mask) return 0u;
   cls = cls_arr[i];
   if (cls == INLET) u0 = R(uin[unsigned(y) + unsigned(g.ny) * unsigned(z)]);
@@ -735,7 +736,7 @@ __device__ __forceinline__ unsigned node_gather(const R* __restrict__ P, const u
     const unsigned k = x == 0 ? i + 1u : i - 1u;
 #pragma unroll
     for (int a = 0; a < L::Q; ++a)
-      if (mask & (1u << a)) f[a] = P[a * g.n + node_src<L>(g, xn, y, z, k, a)];
+      if (mask & (1u << a)) f[a] = P[a * g.n + node_src<L, PER>(g, xn, y, z, k, a)];
     return 0u;
   }
   apply_rules<L, R>(f, mask, cls, u0, rho_out);
@@ -1054,7 +1055,7 @@ struct AdjStep {
 // (node_dst) plus the transposed zero-gradient copies, the transposed
 // collision and blend (Eqs. 30-35) and the transposed boundary rule
 // (Eqs. 37-39).
-template <class L, class R>
+template <class L, class R, bool PER = true>
 __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<R>& P, int x, int y, int z, unsigned i) {
   const Geo& g = A.geo;
   const R* bnext = P.bnext;
@@ -1072,7 +1073,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
     } else {
 #pragma unroll
       for (int k = 0; k < L::Q; ++k) {
-        const unsigned j = node_dst<L>(g, x, y, z, i, k);
+        const unsigned j = node_dst<L, PER>(g, x, y, z, i, k);
         a[k] = j != kNone ? bnext[k * g.n + j] : R(0);
       }
       // A zero-gradient outlet node j on this x face copied p_k(i) into its
@@ -1093,7 +1094,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
   R f[L::Q];
   uint8_t cls;
   R u0;
-  const unsigned mask = node_gather<L, R>(pprev, A.cls, A.uin, A.ph.rho_out, g, x, y, z, i, f, cls, u0);
+  const unsigned mask = node_gather<L, R, PER>(pprev, A.cls, A.uin, A.ph.rho_out, g, x, y, z, i, f, cls, u0);
   Mom<L, R> M;
   moments<L, R>(f, A.ph, M);
   const R gi = A.gfield[i];
@@ -1204,13 +1205,18 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
 // One adjoint step over every node: grid (ceil(nx / kBlock), ny, nz).  Unlike
 // the forward step it needs no split into inner and face rows: its boundary
 // completion costs no occupancy (measured: one kernel beats the pair).
+// The FP32 D2Q9 instantiations are held to 12 blocks (42 registers) per SM:
+// without the wrap arithmetic the compiler otherwise takes 46.
 template <class L, class R>
-__global__ void __launch_bounds__(kBlock) adj_step_kernel(AdjArgs<R> A) {
+constexpr int adj_min_blocks() { return (L::Q == 9 && sizeof(R) == 4) ? 12 : 1; }
+
+template <class L, class R, bool PER = true>
+__global__ void __launch_bounds__(kBlock, adj_min_blocks<L, R>()) adj_step_kernel(AdjArgs<R> A) {
   pdl_enter();
   const Geo& g = A.geo;
   const int x = int(blockIdx.x) * kBlock + int(threadIdx.x), y = int(blockIdx.y), z = int(blockIdx.z);
   if (x >= g.nx) return;
-  adjoint_node<L, R>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z,
+  adjoint_node<L, R, PER>(A, AdjStep<R>{A.bnext, A.pprev, A.bout, A.sample, A.terminal}, x, y, z,
                      unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz);
 }
 

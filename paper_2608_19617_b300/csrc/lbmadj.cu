@@ -479,9 +479,13 @@ struct ImplT final : Impl {
         });
   }
 
+  // One adjoint step: one kernel over every row; a lattice without periodic
+  // axes runs the instantiation whose link selects carry no wrap arithmetic.
   void adj(const void* bnext, const void* pprev, void* bout, int sample) override {
     const lbm::AdjArgs<R> A = adj_args(bnext, pprev, bout, sample);
-    launch(lbm::adj_step_kernel<L, R>, sgrid(), c->ls, A);
+    const bool per = c->cfg.periodic[0] || c->cfg.periodic[1] || c->cfg.periodic[2];
+    if (per) launch(lbm::adj_step_kernel<L, R, true>, sgrid(), c->ls, A);
+    else launch(lbm::adj_step_kernel<L, R, false>, sgrid(), c->ls, A);
     c->kernels += 1;
   }
 

@@ -59,15 +59,18 @@ static void check(int nx, int ny, int nz, int px, int py, int pz) {
           CHECK((long long)i < n, "node %u outside", i);
           hit[i] += 1;
           const unsigned mask = node_unknowns<L>(g, x, y, z);
+          if (!px && !py && !pz) CHECK(mask == (node_unknowns<L, false>(g, x, y, z)), "unknowns without wrap");
           for (int a = 0; a < L::Q; ++a) {
             const long long up = nb(g, x, y, z, -L::cx(a), -L::cy(a), -L::cz(a));
             CHECK(((mask >> a) & 1u) == (up < 0 ? 1u : 0u), "unknown mask of a=%d at (%d,%d,%d)", a, x, y, z);
             const unsigned j = node_src<L>(g, x, y, z, i, a);
+            if (!px && !py && !pz) CHECK(j == (node_src<L, false>(g, x, y, z, i, a)), "node_src without wrap");
             CHECK((long long)j < n, "src %u outside (x %d y %d z %d a %d)", j, x, y, z, a);
             if (up < 0) CHECK(j == i, "unknown link a=%d at (%d,%d,%d) reads %u", a, x, y, z, j);
             else CHECK(up == (long long)j, "src of a=%d at (%d,%d,%d): %u, want %lld", a, x, y, z, j, up);
             const long long down = nb(g, x, y, z, L::cx(a), L::cy(a), L::cz(a));
             const unsigned d = node_dst<L>(g, x, y, z, i, a);
+            if (!px && !py && !pz) CHECK(d == (node_dst<L, false>(g, x, y, z, i, a)), "node_dst without wrap");
             CHECK(d == kNone ? down < 0 : down == (long long)d, "dst of a=%d at (%d,%d,%d)", a, x, y, z);
           }
           // a zero-gradient outlet may sit where the unknowns are exactly one x face's:

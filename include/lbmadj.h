@@ -49,7 +49,7 @@ typedef enum {
   LBM_ERR_CUDA = 3,       /* a CUDA runtime call failed                          */
   LBM_ERR_STATE = 4,      /* call out of order (e.g. adjoint before a window)    */
   LBM_ERR_NONFINITE = 5,  /* a density <= 0 or a non-finite value was produced   */
-  LBM_NOT_CONVERGED = 6   /* reserved for drivers that bound the window loop     */
+  LBM_NOT_CONVERGED = 6   /* lbm_run_until_converged reached its window cap       */
 } lbm_status;
 
 enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
@@ -166,6 +166,17 @@ lbm_status lbm_step_window(lbm_ctx* ctx, double* J_window, double* monitor_windo
  * slices are independent.  Errors: LBM_ERR_ARG for D3Q19 or nslices != nz,
  * LBM_ERR_STATE before a window. */
 lbm_status lbm_window_objectives(lbm_ctx* ctx, double* J, double* monitor, size_t nslices);
+
+/* Alg. 1's outer loop: windows of lbm_step_window until the consecutive-window
+ * test of Eq. 26 holds (converged = ratio < conv_tol between the last two
+ * windows; a window never converges on its own), at most max_windows of them.
+ * Returns the number of windows run and the last window's means and ratio
+ * (each pointer may be NULL).  LBM_OK when the test held; LBM_NOT_CONVERGED
+ * when the cap was reached first, the flow advanced and the last window
+ * recorded, so lbm_adjoint_window may still follow.  Errors of
+ * lbm_step_window stop the loop and are returned as they are. */
+lbm_status lbm_run_until_converged(lbm_ctx* ctx, int32_t max_windows, int32_t* windows, double* J_window,
+                                   double* monitor_window, double* ratio);
 
 /* Consecutive-window test of Eq. 26 between the last two windows:
  * ratio = |(M_i - M_{i-1}) / M_i| (absolute difference when |M_i| < 1e-30),

@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         "lbm_mma_update": (st, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
         "lbm_mma_destroy": (st, [c_void_p]),
         "lbm_get_schedule": (st, [c_void_p, POINTER(LbmSchedule)]),
+        "lbm_run_until_converged": (st, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_double), POINTER(c_double),
+                                         POINTER(c_double)]),
         "lbm_step_window_noalloc": (st, [POINTER(LbmConfig), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
         "lbm_status_string": (ctypes.c_char_p, [c_int32]),
@@ -332,6 +334,16 @@ class Solver:
             if conv:
                 break
         return rec
+
+    def run_windows(self, max_windows=None):
+        """Alg. 1 outer loop in the library (lbm_run_until_converged): returns
+        (windows run, J, monitor, ratio, converged)."""
+        mw = int(max_windows or self.case.max_windows)
+        w, J, M, r = c_int32(), c_double(), c_double(), c_double()
+        st = lib().lbm_run_until_converged(self.ctx, mw, byref(w), byref(J), byref(M), byref(r))
+        if st not in (LBM_OK, LBM_NOT_CONVERGED):
+            check(st, "lbm_run_until_converged")
+        return w.value, J.value, M.value, r.value, st == LBM_OK
 
     def close(self):
         if getattr(self, "ctx", None):

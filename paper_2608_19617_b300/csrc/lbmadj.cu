@@ -988,6 +988,26 @@ lbm_status lbm_step_window(lbm_ctx* c, double* J_window, double* monitor_window)
   return LBM_OK;
 }
 
+lbm_status lbm_run_until_converged(lbm_ctx* c, int32_t max_windows, int32_t* windows, double* J_window,
+                                   double* monitor_window, double* ratio) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  if (max_windows < 1) return fail(LBM_ERR_ARG, "max_windows must be >= 1");
+  double J = 0, M = 0;
+  int32_t w = 0;
+  while (w < max_windows) {
+    LBM_TRY(lbm_step_window(c, &J, &M));
+    w += 1;
+    if (c->converged) break;
+  }
+  if (windows) *windows = w;
+  if (J_window) *J_window = J;
+  if (monitor_window) *monitor_window = M;
+  if (ratio) *ratio = c->ratio;
+  if (!c->converged)
+    return fail(LBM_NOT_CONVERGED, "Eq. 26 did not hold within %d windows (last ratio %.3e)", max_windows, c->ratio);
+  return LBM_OK;
+}
+
 lbm_status lbm_step_window_along(lbm_ctx* c, lbm_ctx* ref, double* J_window, double* monitor_window) {
   if (!c || !ref) return fail(LBM_ERR_ARG, "null context");
   if (c == ref) return fail(LBM_ERR_ARG, "the reference must be another context");

@@ -546,3 +546,23 @@ def test_finite_difference_protocol_as_one_batch():
         (d1, h1), (d2, h2) = d
         fd = (h1 * h1 * d2 - h2 * h2 * d1) / (h1 * h1 - h2 * h2)
         assert abs(fd - grad0[y, x]) <= 1e-6 * abs(grad0[y, x]), (y, x, fd, grad0[y, x])
+
+
+def test_outer_loop_in_the_library_matches_window_by_window():
+    """lbm_run_until_converged (Alg. 1's outer loop) gives the windows, means and
+    ratio of calling lbm_step_window one window at a time, returns
+    LBM_NOT_CONVERGED at its cap, and leaves a recorded window the adjoint can
+    follow."""
+    case = f32_inputs(I.small_channel(140, 12, window_len=15, outlet=I.OUTLET_P, tau=0.53))
+    ref = B.Solver(case, B.LBM_FP64)
+    rec = ref.run_until_converged(max_windows=40)
+    sol = B.Solver(case, B.LBM_FP64)
+    w, J, M, ratio, conv = sol.run_windows(40)
+    assert w == len(rec) and J == rec[-1]["J"] and M == rec[-1]["M"]
+    assert conv == rec[-1]["converged"] and ratio == rec[-1]["ratio"]
+    capped = B.Solver(case, B.LBM_FP64)
+    w1, J1, _, r1, conv1 = capped.run_windows(1)
+    assert w1 == 1 and not conv1 and r1 == float("inf") and J1 == rec[0]["J"]
+    assert "did not hold" in B.last_error()
+    capped.adjoint_window()
+    assert np.abs(capped.design_gradient()).max() > 0

@@ -1205,10 +1205,15 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
 // One adjoint step over every node: grid (ceil(nx / kBlock), ny, nz).  Unlike
 // the forward step it needs no split into inner and face rows: its boundary
 // completion costs no occupancy (measured: one kernel beats the pair).
-// The FP32 D2Q9 instantiations are held to 12 blocks (42 registers) per SM:
-// without the wrap arithmetic the compiler otherwise takes 46.
+// Resident blocks per SM the adjoint step is compiled for, i.e. its register
+// budget (65536 / (128 blocks)): FP32 D2Q9 12 (42 registers; left alone the
+// non-periodic instantiation takes 46), FP32 D3Q19 9 (56), FP64 5 (102).  A
+// minimum of 1 block lets the compiler spend up to 93 registers on the FP32
+// D3Q19 kernel, which then runs at 7 blocks per SM and about 25% slower.
 template <class L, class R>
-constexpr int adj_min_blocks() { return (L::Q == 9 && sizeof(R) == 4) ? 12 : 1; }
+constexpr int adj_min_blocks() {
+  return sizeof(R) == 4 ? (L::Q == 9 ? 12 : 9) : 5;
+}
 
 template <class L, class R, bool PER = true>
 __global__ void __launch_bounds__(kBlock, adj_min_blocks<L, R>()) adj_step_kernel(AdjArgs<R> A) {

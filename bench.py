@@ -43,6 +43,10 @@ WORKLOAD = "ubend384x192x192"
 CKPT_NAMES = ["fp32", "fp16", "bf16", "moment"]   # lbm_config.ckpt_format
 KERNEL_SRC = os.path.join(ROOT, "paper_2608_19617_b300", "csrc", "kernels.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FP64_OPS_FILE = os.path.join(ROOT, "profiles", "fp64_ops.json")
+# FP64 thread-instructions an SM issues per clock on B300: the nominal 1.25
+# TFLOP/s over 148 SMs at 2032 MHz is 2.08 flops per SM per clock, one FMA pair.
+FP64_INST_PER_SM_CLK = 2
 
 
 def parse():
@@ -264,6 +268,54 @@ def unit_traffic(unit, case):
     ks = FWD_KERNELS if unit == "forward step" else ADJ_KERNELS
     v = [measured_traffic(k, case) for k in ks]
     return None if None in v else sum(v)
+
+
+def fp64_inst_per_lu(unit, case):
+    """FP64 thread-instructions (DADD + DMUL + DFMA) per lattice update of one
+    launch of a step in FP64, from the ncu counts in profiles/fp64_ops.json
+    (forward: its two kernels; adjoint: its kernel); None without a capture of
+    the current kernel source."""
+    try:
+        t = json.load(open(FP64_OPS_FILE))
+    except (OSError, ValueError):
+        return None
+    lat = f"D{2 if case.lattice == 9 else 3}Q{case.lattice}"
+    ks = FWD_KERNELS if unit == "forward step" else ADJ_KERNELS
+    v = {e["kernel"]: e["inst_per_lu"] for e in t.get("entries", [])
+         if e.get("lattice") == lat and e.get("source_hash") == kernel_hash()}
+    return sum(v[k] for k in ks) if all(k in v for k in ks) else None
+
+
+def fp64_alu_roofline(roof, kernels, dom, n, clocks):
+    """The roofline of an FP64 run: B300 issues FP64 arithmetic at
+    FP64_INST_PER_SM_CLK thread-instructions per SM per clock, about 1/64 of
+    its FP32 rate, so an FP64 step is bound by that pipe, not by HBM.  achieved
+    = the dominant step's FP64 instructions per launch (ncu counts per node x
+    nodes) over its event-timed duration; peak = SMs x 2 x the maximum SM
+    clock.  The HBM figures stay beside it under "hbm"."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2032.0
+    peak = sms * FP64_INST_PER_SM_CLK * mhz / 1e3          # G instructions / s
+    case = kernels[dom]["case"]
+    ipl = fp64_inst_per_lu(dom, case)
+    hbm = {k_: roof[k_] for k_ in ("achieved", "peak", "unit", "frac", "traffic", "peak_kind")}
+    out = dict(roof)
+    out.update({"bound": "alu", "unit": "G FP64 inst/s", "peak": peak,
+                "peak_kind": f"derived: {sms} SMs x {FP64_INST_PER_SM_CLK} FP64 thread-instructions per clock x "
+                             f"{mhz:.0f} MHz (maximum SM clock)",
+                "inst_per_lu": ipl, "hbm": hbm})
+    if ipl is None:
+        out.update({"achieved": None, "frac": None})
+    else:
+        ach = ipl * n / (kernels[dom]["us"] / 1e6) / 1e9
+        out.update({"achieved": ach, "frac": ach / peak})
+        for k_, v in kernels.items():
+            i_ = fp64_inst_per_lu(k_, case)
+            if i_ is not None:
+                out["kernels"][k_]["fp64_ginst_s"] = i_ * n / (v["us"] / 1e6) / 1e9
+                out["kernels"][k_]["fp64_frac"] = out["kernels"][k_]["fp64_ginst_s"] / peak
+    return out
 
 
 def peaks():
@@ -632,6 +684,11 @@ def run_ours(args, case, rank, world, local):
                                    "design_bytes_per_lu": sweep_b / n, "gbs_design_count": sweep_b / (sweep_us / 1e6) / 1e9,
                                    "frac_design_count": sweep_b / (sweep_us / 1e6) / 1e9 / hbm},
             "phases": phase_rows}
+    clocks = clk.summary()
+    if rs == 8:
+        for v in kernels.values():
+            v["case"] = case
+        roof = fp64_alu_roofline(roof, kernels, dom, n, clocks)
 
     # Accuracy beside the number: the FP32 (or mixed-precision) window and
     # adjoint against the FP64 GPU path on the same trajectory.  The FP64
@@ -709,7 +766,7 @@ def run_ours(args, case, rank, world, local):
         "e2e": (None if e2e_value is None else
                 {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n}),
         "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "error": err,
         "protocol": protocol,
     }

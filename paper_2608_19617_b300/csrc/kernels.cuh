@@ -222,6 +222,45 @@ HD unsigned same_x_neighbour(const Geo& g, int y, int z, unsigned i, int dy, int
   return j;
 }
 
+// Rows (y, z) of the x = 0 (face 0) and x = nx-1 (face 1) planes whose node
+// may have lent a population to a zero-gradient outlet node on the same
+// face (same_x_neighbour): the bounding box of that face's outlet nodes grown
+// by one node, the whole axis where it is periodic; empty (y0 > y1) without
+// outlets.  Only those rows run the adjoint's pull-back of the copies.
+struct ZgRows {
+  int f[2][4];   // per face: y0, y1, z0, z1 (inclusive)
+};
+
+inline ZgRows zg_rows(const uint8_t* cls, const Geo& g) {
+  ZgRows r;
+  for (int f = 0; f < 2; ++f) {
+    r.f[f][0] = r.f[f][2] = 1 << 30;
+    r.f[f][1] = r.f[f][3] = -(1 << 30);
+    const int x = f == 0 ? 0 : g.nx - 1;
+    if (f == 1 && g.nx == 1) continue;
+    for (int z = 0; z < g.nz; ++z)
+      for (int y = 0; y < g.ny; ++y) {
+        if (cls[size_t(x) + size_t(g.nx) * (size_t(y) + size_t(g.ny) * size_t(z))] != OUTLET_ZG) continue;
+        if (y < r.f[f][0]) r.f[f][0] = y;
+        if (y > r.f[f][1]) r.f[f][1] = y;
+        if (z < r.f[f][2]) r.f[f][2] = z;
+        if (z > r.f[f][3]) r.f[f][3] = z;
+      }
+    if (r.f[f][0] > r.f[f][1]) continue;
+    r.f[f][0] = g.py ? 0 : r.f[f][0] - 1;
+    r.f[f][1] = g.py ? g.ny - 1 : r.f[f][1] + 1;
+    r.f[f][2] = g.pz ? 0 : r.f[f][2] - 1;
+    r.f[f][3] = g.pz ? g.nz - 1 : r.f[f][3] + 1;
+  }
+  return r;
+}
+
+// Node (x, y, z) lies on an x face within that face's ZgRows box.
+HD bool zg_row(const ZgRows& r, const Geo& g, int x, int y, int z) {
+  const int f = x == 0 ? 0 : (x == g.nx - 1 ? 1 : -1);
+  return f >= 0 && y >= r.f[f][0] && y <= r.f[f][1] && z >= r.f[f][2] && z <= r.f[f][3];
+}
+
 // The forward step runs two kernels on disjoint rows: the inner rows
 // (1 <= y <= ny-2 and, in 3D, 1 <= z <= nz-2; every slice of a D2Q9 batch),
 // whose only links from outside the domain are those of the x = 0 and
@@ -939,7 +978,7 @@ struct AdjArgs {
   int sample;
   int terminal;                  // 1: b^{n+1} = 0 (last step of the window)
   int dbox[6];                   // design box
-  int zg;                        // 1 if the lattice has zero-gradient outlet nodes
+  ZgRows zg;                     // x-face rows next to zero-gradient outlet nodes
 };
 
 // Transposed boundary completion at a face node (in place on b).
@@ -1077,8 +1116,10 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
         a[k] = j != kNone ? bnext[k * g.n + j] : R(0);
       }
       // A zero-gradient outlet node j on this x face copied p_k(i) into its
-      // unknown f_k(j), j = i + c_k - n_in: pull those adjoints back.
-      if (A.zg && !g.px && (x == 0 || x == g.nx - 1)) {
+      // unknown f_k(j), j = i + c_k - n_in: pull those adjoints back.  Only
+      // the rows next to outlet nodes look (an x-face thread on any other row
+      // would hold its block for the class and adjoint loads).
+      if (zg_row(A.zg, g, x, y, z)) {
         const int sx = x == 0 ? 1 : -1;
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {

@@ -241,7 +241,7 @@ struct lbm_ctx {
   cudaEvent_t fork_cur = nullptr, join_cur = nullptr;
   bool use_graphs = true;
   bool use_pdl = true;        // programmatic dependent launch of the step kernels
-  bool has_zg = false;        // some node is a zero-gradient outlet
+  lbm::ZgRows zg{};           // x-face rows next to zero-gradient outlet nodes
   int64_t kernels = 0;        // kernel launches enqueued so far
   int64_t kernels_window = 0, kernels_adjoint = 0;   // per window / per adjoint sweep, as last enqueued
   lbm_ctx* along = nullptr;   // lbm_step_window_along: the context whose checkpoints start each segment
@@ -461,7 +461,7 @@ struct ImplT final : Impl {
     A.sample = sample;
     A.terminal = bnext == nullptr;
     for (int i = 0; i < 6; ++i) A.dbox[i] = c->cfg.design_box[i];
-    A.zg = c->has_zg ? 1 : 0;
+    A.zg = c->zg;
     return A;
   }
   // One forward step: the inner rows and the face rows concurrently (a
@@ -884,7 +884,7 @@ lbm_status lbm_create(const lbm_config* cfg, const uint8_t* node_class, const fl
   CUDA_TRY(cudaMemsetAsync(x->at(lay.acc), 0, sizeof(lbm::WindowAcc), s));
   CUDA_TRY(cudaMemsetAsync(x->at(lay.flags), 0, 16, s));
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.cls), node_class, n, cudaMemcpyDefault, s));
-  for (size_t k = 0; k < n && !x->has_zg; ++k) x->has_zg = node_class[k] == LBM_OUTLET_ZEROGRAD;
+  x->zg = lbm::zg_rows(node_class, x->geo);
   CUDA_TRY(cudaMemcpyAsync(x->at(lay.gamma), design_gamma, n * 4, cudaMemcpyDefault, s));
   if (objective_weights) CUDA_TRY(cudaMemcpyAsync(x->at(lay.wobj), objective_weights, n * 4, cudaMemcpyDefault, s));
   else CUDA_TRY(cudaMemsetAsync(x->at(lay.wobj), 0, n * 4, s));

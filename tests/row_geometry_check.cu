@@ -5,7 +5,9 @@
 // links are those from outside the domain, that every population index the
 // pulls, the zero-gradient copies and the adjoint's same-face lookups read
 // lies in the lattice and is the node the geometry names, and that every
-// block-sum slot lies in its range (a D2Q9 slice's blocks contiguous).
+// block-sum slot lies in its range (a D2Q9 slice's blocks contiguous), and
+// that the rows running the adjoint's zero-gradient pull-back cover every
+// node an outlet copied from.
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -184,6 +186,45 @@ static void check_split(int nx, int ny, int nz, int px, int py, int pz) {
   for (long long k = 0; k < nslot; ++k) CHECK(slot[size_t(k)] == 1, "slot %lld used %d times", k, slot[size_t(k)]);
 }
 
+// The rows that run the adjoint's zero-gradient pull-back (zg_row over
+// zg_rows of the class map) include every x-face node with a same-face
+// neighbour that is a zero-gradient outlet, on class maps with outlet nodes
+// at random places on both x faces (bounded x axis, as validated).
+template <class L>
+static void check_zg(int nx, int ny, int nz, int py, int pz, unsigned seed, int density) {
+  const Geo g{nx, ny, nz, 0, py, pz, unsigned(nx * ny * nz), unsigned(nx), unsigned(nx * ny)};
+  std::vector<uint8_t> cls(size_t(nx) * ny * nz, FLUID);
+  unsigned h = seed;
+  int nzg = 0;
+  for (int f = 0; f < 2; ++f)
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y) {
+        h = h * 1664525u + 1013904223u;
+        if (int((h >> 16) % 100) < density) {
+          cls[size_t(f ? nx - 1 : 0) + size_t(nx) * (size_t(y) + size_t(ny) * z)] = OUTLET_ZG;
+          ++nzg;
+        }
+      }
+  const ZgRows r = zg_rows(cls.data(), g);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const unsigned i = unsigned(x) + unsigned(y) * g.sy + unsigned(z) * g.sz;
+        const bool row = zg_row(r, g, x, y, z);
+        if (x != 0 && x != nx - 1) { CHECK(!row, "zg row off the x faces at (%d,%d,%d)", x, y, z); continue; }
+        if (!nzg) CHECK(!row, "zg row without outlets at (%d,%d,%d)", x, y, z);
+        const int sx = x == 0 ? 1 : -1;
+        for (int k = 0; k < L::Q; ++k) {
+          if (L::cx(k) != sx) continue;
+          const unsigned j = same_x_neighbour(g, y, z, i, L::cy(k), L::cz(k));
+          if (j == kNone) continue;
+          if (cls[j] == OUTLET_ZG)
+            CHECK(row, "node (%d,%d,%d) lends link %d to an outlet but is outside the zg rows (shape %d %d %d)",
+                  x, y, z, k, nx, ny, nz);
+        }
+      }
+}
+
 int main() {
   const int per[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {1, 1, 1}};
   const int shapes3[][3] = {{3, 3, 3}, {5, 4, 3}, {130, 6, 5}, {128, 3, 4}, {129, 7, 6}, {256, 5, 3}, {7, 3, 130}};
@@ -213,6 +254,14 @@ int main() {
   check_split<D2Q9>(1, 5, 1, 1, 0, 0);
   check_split<D2Q9>(6, 1, 3, 0, 1, 0);
   check_split<D2Q9>(2, 2, 2, 1, 1, 0);
+  const int zgshape3[][3] = {{3, 3, 3}, {5, 9, 7}, {130, 12, 10}, {4, 40, 3}};
+  const int zgshape2[][3] = {{3, 3, 1}, {10, 17, 1}, {131, 9, 3}};
+  for (int py = 0; py < 2; ++py)
+    for (int pz = 0; pz < 2; ++pz)
+      for (int d : {0, 1, 5, 30, 100}) {
+        for (auto& s : zgshape3) check_zg<D3Q19>(s[0], s[1], s[2], py, pz, 17u + unsigned(d), d);
+        for (auto& s : zgshape2) check_zg<D2Q9>(s[0], s[1], s[2], py, 0, 29u + unsigned(d), d);
+      }
   printf("%s (%d failures)\n", failures ? "FAILED" : "ok", failures);
   return failures ? 1 : 0;
 }

@@ -201,18 +201,20 @@ def kernel_hash():
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def measured_traffic(kernel, case):
+def measured_traffic(kernel, case, precision="fp32"):
     """DRAM bytes per launch of kernel on this workload from profiles/traffic.json:
     an ncu capture of the workload itself, or of a smaller lattice of the same
     family listed as scaling to it (bytes per node x this lattice's nodes;
     DRAM traffic of a step grows with the node count).  None without a
-    capture of the current kernel source."""
+    capture of the current kernel source in this precision."""
     try:
         t = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
     for e in t.get("entries", []):
         if e.get("kernel") != kernel or e.get("source_hash") != kernel_hash():
+            continue
+        if e.get("precision", "fp32") != precision:
             continue
         if e.get("workload") == case.name:
             return e.get("bytes_per_launch")
@@ -261,12 +263,12 @@ FWD_KERNELS = ("fwd_row_kernel", "fwd_facerow_kernel")
 ADJ_KERNELS = ("adj_step_kernel",)
 
 
-def unit_traffic(unit, case):
+def unit_traffic(unit, case, precision="fp32"):
     """ncu DRAM bytes of one launch of a step (forward: its two kernels;
     adjoint: its kernel), None if a kernel has no capture for the current
-    source."""
+    source in this precision."""
     ks = FWD_KERNELS if unit == "forward step" else ADJ_KERNELS
-    v = [measured_traffic(k, case) for k in ks]
+    v = [measured_traffic(k, case, precision) for k in ks]
     return None if None in v else sum(v)
 
 
@@ -668,7 +670,7 @@ def run_ours(args, case, rank, world, local):
     ach_design = u["bytes"] / (u["us"] / 1e6) / 1e9
     sweep_sv = survey_bytes_per_lu(case, "adjoint sweep step", rs=rs) * n
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": unit_traffic(dom, case),
+            "traffic": unit_traffic(dom, case, "fp64" if rs == 8 else "fp32"),
             "dominant": dom, "kernel": u["kernel"], "bytes_per_launch": sv, "bytes_per_lu": u["survey_bytes_per_lu"],
             "us_per_launch": u["us"], "launches_per_bench_step": u["launches"],
             "design_count": {"bytes_per_launch": u["bytes"], "bytes_per_lu": u["bytes"] / n,

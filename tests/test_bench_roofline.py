@@ -46,6 +46,7 @@ def test_traffic_lookup_scales_and_voids(bench, tmp_path, monkeypatch):
     assert bench.measured_traffic("adj_step_kernel", _case(19, "big", 5000)) == pytest.approx(1.0e6)
     assert bench.measured_traffic("adj_step_kernel", _case(19, "other", 5000)) is None
     assert bench.unit_traffic("forward step", _case(19, "big", 5000)) is None   # no forward entries
+    assert bench.measured_traffic("adj_step_kernel", _case(19, "big", 5000), "fp64") is None   # FP32 capture
     monkeypatch.setattr(bench, "kernel_hash", lambda: "h2")                        # kernel source changed
     assert bench.measured_traffic("adj_step_kernel", _case(19, "big", 5000)) is None
 

@@ -79,12 +79,37 @@ def test_forward_fp32_within_1e5(name):
     assert rel_err(ug, uw) < 1e-5
 
 
+def _periodic_y_channel(nx, ny, **kw):
+    """A 2D channel periodic in y (no walls along x): inlet on x = 0; on
+    x = nx-1 a zero-gradient outlet on rows 0-2 and walls on the other rows.
+    The outlet node on row 0 copies a population of the wall node on row
+    ny-1 across the periodic wrap, so the adjoint must pull it back there."""
+    c = I.small_channel(nx, ny, outlet=I.OUTLET_ZG, **kw)
+    cls = np.zeros_like(c.node_class)
+    cls[0, :, 0] = I.INLET
+    cls[0, :, nx - 1] = I.WALL
+    cls[0, 0:3, nx - 1] = I.OUTLET_ZG
+    gamma = c.gamma.copy()
+    gamma[0, 0, :] = gamma[0, 2, :]
+    gamma[0, ny - 1, :] = gamma[0, ny - 3, :]
+    gamma[cls == I.INLET] = 0.0
+    gamma[cls == I.OUTLET_ZG] = 0.0
+    gamma[cls == I.WALL] = 1.0
+    w = np.zeros_like(c.obj_weights)
+    w[0, :, nx - 4] = 1.0 / ny     # near the outlet, so that the adjoint window reaches it
+    return c.replace(name=f"channel{nx}x{ny}-periodic-y", node_class=cls, gamma=gamma,
+                     inlet_u=np.full((1, ny), 0.05), obj_weights=w, periodic=(0, 1, 0),
+                     design_box=(1, nx - 1, 0, ny, 0, 1))
+
+
 ADJ_CASES = {
     "diss-zouhe": lambda: I.small_channel(150, 12, obj_kind=I.OBJ_DISSIPATION, window_len=12,
                                           outlet=I.OUTLET_P, profile="parabolic", tau=0.53, cs_smag=0.12),
     "veldev-zg-dw3": lambda: I.small_channel(140, 11, obj_kind=I.OBJ_VELOCITY_DEV, window_len=12,
                                              outlet=I.OUTLET_ZG, sample_every=3, tau=0.52),
     "pressure": lambda: I.small_channel(133, 10, obj_kind=I.OBJ_PRESSURE, window_len=10, tau=0.56),
+    "veldev-zg-periodic-y": lambda: _periodic_y_channel(137, 9, obj_kind=I.OBJ_VELOCITY_DEV, window_len=12,
+                                                        sample_every=3, tau=0.53),
     "drag-periodic": lambda: I.small_channel(129, 9, obj_kind=I.OBJ_DRAG, window_len=10,
                                              periodic_x=True, g_max=0.9, monitor_kind=I.MON_OBJECTIVE),
     "d3q19-pressure": lambda: I.small_duct3d(130, 6, 6, window_len=8, tau=0.53),

@@ -10,7 +10,7 @@ to the initial time through every checkpoint segment.  Checked here:
   FP64 build; cosine 0.9999 and 1e-3 norm-wise for FP32);
 * J and the final state equal, bit for bit, a plain window after the same
   unsampled spin-up (same samples, same block sums, same reduction);
-* the persistent and pipelined launch paths;
+* the pipelined launch path;
 * argument and state errors of lbm_set_sample_start.
 """
 import numpy as np

@@ -428,32 +428,45 @@ struct Mom {
   R te, om;                // tau_eff (Eq. 14), 1 - 1/tau_eff
 };
 
-// Add direction a's value v into the running zeroth, first and second
-// moments (rt, m, m2 with entries xx, yy, zz, xy, xz, yz), in the order every
-// kernel uses, so that moments accumulated direction by direction as the
-// loads arrive equal raw_moments() bit for bit.
-template <class L, class R>
-__device__ __forceinline__ void moment_add(int a, R v, R& rt, R (&m)[3], R (&m2)[6]) {
-  const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-  rt += v;
-  if (cx > 0) m[0] += v; else if (cx < 0) m[0] -= v;
-  if (cy > 0) m[1] += v; else if (cy < 0) m[1] -= v;
-  if (cz > 0) m[2] += v; else if (cz < 0) m[2] -= v;
-  if (cx) m2[0] += v;
-  if (cy) m2[1] += v;
-  if (cz) m2[2] += v;
-  if (cx * cy > 0) m2[3] += v; else if (cx * cy < 0) m2[3] -= v;
-  if (cx * cz > 0) m2[4] += v; else if (cx * cz < 0) m2[4] -= v;
-  if (cy * cz > 0) m2[5] += v; else if (cy * cz < 0) m2[5] -= v;
+// Add v into an accumulator; the first contribution sets it (no addition to
+// zero).  In the fully unrolled direction loops `set` is a compile-time
+// constant, so the branch folds away.
+template <class R>
+__device__ __forceinline__ void acc_add(R& x, bool& set, R v) {
+  if (set) x += v; else { x = v; set = true; }
 }
 
 // Zeroth, first and second moments of a population-shaped array, each
-// weighted by wt(a) (1 for f, w_a for adjoints).
+// weighted by wt(a) (1 for f, w_a for adjoints; entries of the second moment
+// xx, yy, zz, xy, xz, yz).  Opposite directions a, abar (a < abar) enter as
+// s = f_a + f_abar and d = f_a - f_abar (w_a = w_abar): the even moments are
+// sums of s, the odd ones signed sums of d, added in a fixed order.
 template <class L, class R, bool W>
 __device__ __forceinline__ void raw_moments(const R (&f)[L::Q], R& m0, R (&m1)[3], R (&m2)[6]) {
-  R rt = 0, m[3] = {0, 0, 0}, q[6] = {0, 0, 0, 0, 0, 0};
+  R rt = W ? mul_rn(R(L::w(0)), f[0]) : f[0];
+  R m[3] = {R(0), R(0), R(0)}, q[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  bool ms[3] = {false, false, false}, qs[6] = {false, false, false, false, false, false};
 #pragma unroll
-  for (int a = 0; a < L::Q; ++a) moment_add<L, R>(a, W ? R(L::w(a)) * f[a] : f[a], rt, m, q);
+  for (int a = 1; a < L::Q; ++a) {
+    const int b = L::opp(a);
+    if (b < a) continue;
+    R s = f[a] + f[b], d = f[a] - f[b];
+    if (W) {
+      s = mul_rn(R(L::w(a)), s);
+      d = mul_rn(R(L::w(a)), d);
+    }
+    const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+    rt += s;
+    if (cx) acc_add(m[0], ms[0], cx > 0 ? d : -d);
+    if (cy) acc_add(m[1], ms[1], cy > 0 ? d : -d);
+    if (cz) acc_add(m[2], ms[2], cz > 0 ? d : -d);
+    if (cx) acc_add(q[0], qs[0], s);
+    if (cy) acc_add(q[1], qs[1], s);
+    if (cz) acc_add(q[2], qs[2], s);
+    if (cx * cy) acc_add(q[3], qs[3], cx * cy > 0 ? s : -s);
+    if (cx * cz) acc_add(q[4], qs[4], cx * cz > 0 ? s : -s);
+    if (cy * cz) acc_add(q[5], qs[5], cy * cz > 0 ? s : -s);
+  }
   m0 = rt;
 #pragma unroll
   for (int k = 0; k < 3; ++k) m1[k] = m[k];
@@ -500,22 +513,32 @@ __device__ __forceinline__ void moments_from_raw(R rt, const R (&m)[3], const R 
   M.om = R(1) - R(1) / M.te;
 }
 
-// Value at direction a of w_a (s0 + s1.c_a + c_a.S2.c_a), S2 symmetric with
-// entries (xx, yy, zz, xy, xz, yz).
+// b_a = s0 + s1.c_a + c_a.S2.c_a for every direction a (S2 symmetric,
+// entries xx, yy, zz, xy, xz, yz).  Opposite directions share the even part
+// s0 + c.S2.c and take the odd part s1.c with opposite signs.
 template <class L, class R>
-__device__ __forceinline__ R quad_form(int a, R s0, const R (&s1)[3], const R (&s2)[6]) {
-  const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-  R v = s0;
-  if (cx) v += cx > 0 ? s1[0] : -s1[0];
-  if (cy) v += cy > 0 ? s1[1] : -s1[1];
-  if (cz) v += cz > 0 ? s1[2] : -s1[2];
-  if (cx) v += s2[0];
-  if (cy) v += s2[1];
-  if (cz) v += s2[2];
-  if (cx * cy) v += cx * cy > 0 ? R(2) * s2[3] : R(-2) * s2[3];
-  if (cx * cz) v += cx * cz > 0 ? R(2) * s2[4] : R(-2) * s2[4];
-  if (cy * cz) v += cy * cz > 0 ? R(2) * s2[5] : R(-2) * s2[5];
-  return v;
+__device__ __forceinline__ void quad_all(R s0, const R (&s1)[3], const R (&s2)[6], R (&out)[L::Q]) {
+  out[0] = s0;
+#pragma unroll
+  for (int a = 1; a < L::Q; ++a) {
+    const int b = L::opp(a);
+    if (b < a) continue;
+    const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+    R e = s0;
+    if (cx) e += s2[0];
+    if (cy) e += s2[1];
+    if (cz) e += s2[2];
+    if (cx * cy) e = fma_rn(cx * cy > 0 ? R(2) : R(-2), s2[3], e);
+    if (cx * cz) e = fma_rn(cx * cz > 0 ? R(2) : R(-2), s2[4], e);
+    if (cy * cz) e = fma_rn(cy * cz > 0 ? R(2) : R(-2), s2[5], e);
+    R o = R(0);
+    bool os = false;
+    if (cx) acc_add(o, os, cx > 0 ? s1[0] : -s1[0]);
+    if (cy) acc_add(o, os, cy > 0 ? s1[1] : -s1[1]);
+    if (cz) acc_add(o, os, cz > 0 ? s1[2] : -s1[2]);
+    out[a] = e + o;
+    out[b] = e - o;
+  }
 }
 
 // Blended post-collision field (Eqs. 16 and 23):
@@ -548,21 +571,35 @@ __device__ __forceinline__ void blend_coefs(const Mom<L, R>& M, R g, Blend<R>& C
   C.X[5] = fma_rn(M.om, M.pi[5], mul_rn(M.m[1], M.u[2]));
 }
 
-// p~_a / w_a from the blend coefficients, fused multiply-adds in a fixed order.
+// p~_a = w_a (a0 + b m.c_a + 4.5 c_a.X.c_a) of every direction, stored at node
+// i of dst ([Q][n]).  Opposite directions share the even part a0 + 4.5 c.X.c
+// (fused multiply-adds in a fixed order) and take the odd part b m.c with
+// opposite signs.  Every kernel that writes or rebuilds a carried field calls
+// this, so they agree bit for bit.
 template <class L, class R>
-__device__ __forceinline__ R blend_value(int a, const Blend<R>& C) {
-  const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-  R v = C.a0;
-  if (cx) v = fma_rn(cx > 0 ? C.b : -C.b, C.m[0], v);
-  if (cy) v = fma_rn(cy > 0 ? C.b : -C.b, C.m[1], v);
-  if (cz) v = fma_rn(cz > 0 ? C.b : -C.b, C.m[2], v);
-  if (cx) v = fma_rn(R(4.5), C.X[0], v);
-  if (cy) v = fma_rn(R(4.5), C.X[1], v);
-  if (cz) v = fma_rn(R(4.5), C.X[2], v);
-  if (cx * cy) v = fma_rn(cx * cy > 0 ? R(9) : R(-9), C.X[3], v);
-  if (cx * cz) v = fma_rn(cx * cz > 0 ? R(9) : R(-9), C.X[4], v);
-  if (cy * cz) v = fma_rn(cy * cz > 0 ? R(9) : R(-9), C.X[5], v);
-  return v;
+__device__ __forceinline__ void blend_store(R* __restrict__ dst, unsigned n, unsigned i, const Blend<R>& C) {
+  dst[i] = mul_rn(R(L::w(0)), C.a0);
+#pragma unroll
+  for (int a = 1; a < L::Q; ++a) {
+    const int b = L::opp(a);
+    if (b < a) continue;
+    const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+    R e = C.a0;
+    if (cx) e = fma_rn(R(4.5), C.X[0], e);
+    if (cy) e = fma_rn(R(4.5), C.X[1], e);
+    if (cz) e = fma_rn(R(4.5), C.X[2], e);
+    if (cx * cy) e = fma_rn(cx * cy > 0 ? R(9) : R(-9), C.X[3], e);
+    if (cx * cz) e = fma_rn(cx * cz > 0 ? R(9) : R(-9), C.X[4], e);
+    if (cy * cz) e = fma_rn(cy * cz > 0 ? R(9) : R(-9), C.X[5], e);
+    R mc = R(0);
+    bool ms = false;
+    if (cx) acc_add(mc, ms, cx > 0 ? C.m[0] : -C.m[0]);
+    if (cy) acc_add(mc, ms, cy > 0 ? C.m[1] : -C.m[1]);
+    if (cz) acc_add(mc, ms, cz > 0 ? C.m[2] : -C.m[2]);
+    const R o = mul_rn(C.b, mc);
+    dst[unsigned(a) * n + i] = mul_rn(R(L::w(a)), e + o);
+    dst[unsigned(b) * n + i] = mul_rn(R(L::w(a)), e - o);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -677,7 +714,7 @@ struct FwdStep {
   R* mom;         // non-null: moment checkpoint of p^n (mom_coefs<L>() planes of n values)
 };
 
-// Moment checkpoints.  The carried field is p~_a = w_a blend_value(a, C) at
+// Moment checkpoints.  The carried field is p~ = blend_store(C) at
 // every node (interior and face alike), so the coefficients C as the step
 // computed them regenerate p~ exactly: a0, b, m (D values) and X (D(D+1)/2),
 // 7 planes in 2D and 11 in 3D instead of Q.
@@ -739,9 +776,7 @@ __device__ __forceinline__ void forward_core(const FwdArgs<R>& A, const FwdStep<
   Blend<R> C;
   blend_coefs<L, R>(M, gi, C);
   if constexpr (MOM) store_coefs<L, R>(P.mom, g.n, i, C);
-  R* dst = P.dst;
-#pragma unroll
-  for (int a = 0; a < L::Q; ++a) dst[a * g.n + i] = mul_rn(R(L::w(a)), blend_value<L, R>(a, C));
+  blend_store<L, R>(P.dst, g.n, i, C);
   if (P.sample) {
     const int* b = A.obj.box;
     if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {
@@ -1233,8 +1268,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<R>& A, const AdjStep<
   }
   // b_a = d psi / d f_a = grho + c_a . gm + c_a c_a : cpi
   R b[L::Q];
-#pragma unroll
-  for (int k = 0; k < L::Q; ++k) b[k] = quad_form<L, R>(k, grho, gm, cpi);
+  quad_all<L, R>(grho, gm, cpi, b);
   if (mask) bc_transpose<L, R>(b, mask, cls, u0);
 #pragma unroll
   for (int k = 0; k < L::Q; ++k) bout[k * g.n + i] = b[k];
@@ -1319,7 +1353,7 @@ __global__ void gradient_kernel(const double2* __restrict__ gacc, const float* _
   }
 }
 
-// Moment checkpoint -> p~ at every node: w_a blend_value(a, C), the step
+// Moment checkpoint -> p~ at every node through blend_store(), the step
 // kernels' own arithmetic, so the field is bitwise the one the step stored.
 template <class L, class R>
 __global__ void __launch_bounds__(kBlock) mom_decode_kernel(const R* __restrict__ mom, R* __restrict__ p, unsigned n) {
@@ -1327,8 +1361,7 @@ __global__ void __launch_bounds__(kBlock) mom_decode_kernel(const R* __restrict_
   if (i >= n) return;
   Blend<R> C;
   load_coefs<L, R>(mom, n, i, C);
-#pragma unroll
-  for (int a = 0; a < L::Q; ++a) p[a * n + i] = mul_rn(R(L::w(a)), blend_value<L, R>(a, C));
+  blend_store<L, R>(p, n, i, C);
 }
 
 template <class L, class R>

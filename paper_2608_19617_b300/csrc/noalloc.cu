@@ -128,8 +128,7 @@ __global__ void __launch_bounds__(lbm::kBlock) fwd_step_noalloc_kernel(lbm::FwdA
     const float gi = float(g_max * (1.0 - phi * (1.0 + q) / (phi + q)));
     Blend<float> C;
     blend_coefs<L, float>(M, gi, C);
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) A.dst[a * g.n + i] = mul_rn(float(L::w(a)), blend_value<L, float>(a, C));
+    blend_store<L, float>(A.dst, g.n, i, C);
     if (A.sample) {
       const int* b = A.obj.box;
       if (x >= b[0] && x < b[1] && y >= b[2] && y < b[3] && z >= b[4] && z < b[5]) {

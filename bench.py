@@ -180,7 +180,7 @@ def bytes_per_lu(case, phase, rs=4):
     return (3 * q + 1) * rs + 2.0 * rs * nd / n + 4.0 * no / n / case.sample_every
 
 
-def survey_bytes_per_lu(case, unit, rs=4):
+def scope_bytes_per_lu(case, unit, rs=4):
     """The scope table's algorithmic bytes per lattice update of a unit of
     work: forward (2Q + 1) 4 B (D2Q9 76, D3Q19 156; FP64 148 / 308); adjoint
     sweep step = adjoint kernel (12Q + 4 + 32 B: two population reads, one
@@ -655,9 +655,9 @@ def run_ours(args, case, rank, world, local):
     kernels = {
         "forward step": {"kernel": fk, "us": fwd_us, "launches": W + S * (K - 1),
                          "bytes": bytes_per_lu(case, "forward", rs=rs) * n,
-                         "survey_bytes_per_lu": survey_bytes_per_lu(case, "forward step", rs=rs)},
+                         "scope_bytes_per_lu": scope_bytes_per_lu(case, "forward step", rs=rs)},
         "adjoint step": {"kernel": ak, "us": adj_us, "launches": W, "bytes": bytes_per_lu(case, "adjoint", rs=rs) * n,
-                         "survey_bytes_per_lu": (12 * case.lattice + 4 + 32) * rs // 4,
+                         "scope_bytes_per_lu": (12 * case.lattice + 4 + 32) * rs // 4,
                          "timing": "adjoint phase events (serial sweep)" if serial
                                    else "sweep step less its recompute share (pipelined sweep)"},
     }
@@ -665,13 +665,13 @@ def run_ours(args, case, rank, world, local):
         v["ms_per_bench_step"] = v["us"] * v["launches"] / 1e3
     dom = max(kernels, key=lambda k_: kernels[k_]["ms_per_bench_step"])
     u = kernels[dom]
-    sv = u["survey_bytes_per_lu"] * n      # the scope table's count for one launch
+    sv = u["scope_bytes_per_lu"] * n      # the scope table's count for one launch
     ach = sv / (u["us"] / 1e6) / 1e9
     ach_design = u["bytes"] / (u["us"] / 1e6) / 1e9
-    sweep_sv = survey_bytes_per_lu(case, "adjoint sweep step", rs=rs) * n
+    sweep_sv = scope_bytes_per_lu(case, "adjoint sweep step", rs=rs) * n
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": unit_traffic(dom, case, "fp64" if rs == 8 else "fp32"),
-            "dominant": dom, "kernel": u["kernel"], "bytes_per_launch": sv, "bytes_per_lu": u["survey_bytes_per_lu"],
+            "dominant": dom, "kernel": u["kernel"], "bytes_per_launch": sv, "bytes_per_lu": u["scope_bytes_per_lu"],
             "us_per_launch": u["us"], "launches_per_bench_step": u["launches"],
             "design_count": {"bytes_per_launch": u["bytes"], "bytes_per_lu": u["bytes"] / n,
                              "achieved": ach_design, "frac": ach_design / hbm},
@@ -679,9 +679,9 @@ def run_ours(args, case, rank, world, local):
             "timing": "CUDA events on the library stream inside the timed region: per forward-window phase, and "
                       "around each whole adjoint sweep",
             "kernels": {k_: {"us": v["us"], "launches": v["launches"], "ms_per_bench_step": v["ms_per_bench_step"],
-                             "gbs": v["survey_bytes_per_lu"] * n / (v["us"] / 1e6) / 1e9,
+                             "gbs": v["scope_bytes_per_lu"] * n / (v["us"] / 1e6) / 1e9,
                              "gbs_design_count": v["bytes"] / (v["us"] / 1e6) / 1e9} for k_, v in kernels.items()},
-            "adjoint_sweep_step": {"us": sweep_us, "survey_bytes_per_lu": survey_bytes_per_lu(case, "adjoint sweep step", rs=rs),
+            "adjoint_sweep_step": {"us": sweep_us, "scope_bytes_per_lu": scope_bytes_per_lu(case, "adjoint sweep step", rs=rs),
                                    "gbs": sweep_sv / (sweep_us / 1e6) / 1e9, "frac": sweep_sv / (sweep_us / 1e6) / 1e9 / hbm,
                                    "design_bytes_per_lu": sweep_b / n, "gbs_design_count": sweep_b / (sweep_us / 1e6) / 1e9,
                                    "frac_design_count": sweep_b / (sweep_us / 1e6) / 1e9 / hbm},

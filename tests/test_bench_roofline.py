@@ -29,10 +29,10 @@ def test_scope_byte_counts(bench):
     adjoint sweep 256 / 496 B, twice that in FP64."""
     for q, fwd, sweep in ((9, 76, 256), (19, 156, 496)):
         c = _case(q, "x", 1)
-        assert bench.survey_bytes_per_lu(c, "forward step") == fwd == (2 * q + 1) * 4
-        assert bench.survey_bytes_per_lu(c, "forward step", rs=8) == 2 * q * 8 + 4
-        assert bench.survey_bytes_per_lu(c, "adjoint sweep step") == sweep
-        assert bench.survey_bytes_per_lu(c, "adjoint sweep step", rs=8) == 2 * sweep
+        assert bench.scope_bytes_per_lu(c, "forward step") == fwd == (2 * q + 1) * 4
+        assert bench.scope_bytes_per_lu(c, "forward step", rs=8) == 2 * q * 8 + 4
+        assert bench.scope_bytes_per_lu(c, "adjoint sweep step") == sweep
+        assert bench.scope_bytes_per_lu(c, "adjoint sweep step", rs=8) == 2 * sweep
 
 
 def test_traffic_lookup_scales_and_voids(bench, tmp_path, monkeypatch):

@@ -306,6 +306,77 @@ def test_full_size_one_step_against_oracle(name):
     assert np.abs(got - want).max() < 2e-6
 
 
+def _x_crop(case, x0, x1):
+    """Columns x0 .. x1-1 of a lattice as a lattice of its own, the cut faces
+    made walls.  One step of a node at least one column away from a cut pulls
+    the same populations as in the whole lattice."""
+    cls = case.node_class[:, :, x0:x1].copy()
+    if x0 > 0:
+        cls[:, :, 0] = I.WALL
+    if x1 < case.nx:
+        cls[:, :, -1] = I.WALL
+    uin = case.inlet_u if x0 == 0 else np.zeros_like(case.inlet_u)
+    return case.replace(name=f"{case.name}[x{x0}:{x1}]", nx=x1 - x0, node_class=cls,
+                        gamma=case.gamma[:, :, x0:x1].copy(), inlet_u=uin,
+                        obj_weights=case.obj_weights[:, :, x0:x1].copy(),
+                        design_box=(1, x1 - x0 - 1, 1, case.ny - 1, 1, case.nz - 1))
+
+
+def test_default_workload_one_step_against_oracle_on_crops():
+    """The 384x192x192 U-bend (the benchmark's default workload): after a
+    spin-up, one GPU step over the whole lattice in the benchmark's launch
+    configuration equals, element by element, the oracle's step on two
+    64-column crops of the same field -- the x = 0 end (velocity inlet and
+    zero-gradient outlet side by side, the legs) and the far end (the bend) --
+    at every node but the crops' cut faces."""
+    case = f32_inputs(I.WORKLOADS["ubend384x192x192"]()).replace(window_len=20, ckpt_every=10)
+    sol = B.Solver(case, B.LBM_FP32)
+    sol.advance(300)
+    q, nx, ny, nz = case.lattice, case.nx, case.ny, case.nz
+    p = sol.get_state().reshape(q, nz, ny, nx)
+    sol.advance(1)
+    got = sol.get_state().reshape(q, nz, ny, nx)
+    sol.close()
+    for x0, x1 in ((0, 64), (320, 384)):
+        crop = _x_crop(case, x0, x1)
+        want = oracle_advance(O.Problem(crop), p[:, :, :, x0:x1].reshape(q, -1), 1).reshape(q, nz, ny, x1 - x0)
+        lo, hi = (1 if x0 > 0 else 0), (x1 - x0 - 1 if x1 < nx else x1 - x0)
+        diff = np.abs(got[:, :, :, x0 + lo:x0 + hi] - want[:, :, :, lo:hi])
+        assert diff.max() < 2e-6, (x0, x1, float(diff.max()))
+
+
+def test_default_workload_two_step_adjoint_against_oracle_on_a_crop():
+    """The 384x192x192 U-bend, design box widened to the whole duct: a
+    two-step window and its adjoint over the whole lattice, against the
+    oracle's on the 12 columns around the objective planes (x = 48).  In two
+    steps the adjoint of the plane's samples reaches two columns to each side,
+    so J, the gradient and the start-field adjoint of the columns away from the
+    cuts are those of the whole lattice."""
+    case = f32_inputs(I.WORKLOADS["ubend384x192x192"]()).replace(window_len=2, ckpt_every=2,
+                                                                design_box=(1, 383, 1, 191, 1, 191))
+    q, nx, ny, nz = case.lattice, case.nx, case.ny, case.nz
+    sol = B.Solver(case, B.LBM_FP32)
+    sol.advance(300)
+    p0 = sol.get_state().reshape(q, nz, ny, nx)
+    J, _ = sol.step_window()
+    sol.adjoint_window()
+    grad = sol.design_gradient().reshape(nz, ny, nx)
+    a0 = sol.get_adjoint_state().reshape(q, nz, ny, nx)
+    sol.close()
+    x0, x1 = 42, 54
+    crop = _x_crop(case, x0, x1)
+    pr = O.Problem(crop)
+    _, Jw, _, traj = pr.run_window(p0[:, :, :, x0:x1].reshape(q, -1))
+    _, grad_w, a0_w = pr.adjoint_window(traj)
+    assert abs(J - Jw) <= 1e-4 * abs(Jw)
+    g, gw = grad[:, :, x0 + 1:x1 - 1], grad_w.reshape(nz, ny, x1 - x0)[:, :, 1:-1]
+    a, aw = a0[:, :, :, x0 + 1:x1 - 1], a0_w.reshape(q, nz, ny, x1 - x0)[:, :, :, 1:-1]
+    assert np.count_nonzero(gw) > 0 and np.count_nonzero(aw) > 0
+    assert cosine(g, gw) > 0.9999 and rel_err(g, gw) < 1e-3
+    assert cosine(a, aw) > 0.9999 and rel_err(a, aw) < 1e-3
+    assert np.all(grad[:, :, :x0 + 2] == 0) and np.all(grad[:, :, x1 - 2:] == 0)   # beyond the adjoint's reach
+
+
 def test_channel_workload_fp64_at_full_size_against_oracle():
     """The 128x64 channel workload (parabolic Zou-He inlet, zero-gradient
     outlet, disk plus noise, FP64): 200 steps from rest against the oracle,

@@ -345,36 +345,60 @@ def test_default_workload_one_step_against_oracle_on_crops():
         assert diff.max() < 2e-6, (x0, x1, float(diff.max()))
 
 
-def test_default_workload_two_step_adjoint_against_oracle_on_a_crop():
-    """The 384x192x192 U-bend, design box widened to the whole duct: a
+# Columns around each objective plane: ubend256 and ubend384 sample the
+# pressure drop on x = 32 / 48, step2048x512 on x = 8 and x = nx - 9.
+FULL_SIZE_ADJOINT_CROPS = {
+    "ubend256x128x64": [(26, 38)],
+    "ubend384x192x192": [(42, 54)],
+    "step2048x512": [(0, 14), (2034, 2048)],
+}
+
+
+@pytest.mark.parametrize("name", list(FULL_SIZE_ADJOINT_CROPS))
+def test_full_size_two_step_adjoint_against_oracle_on_crops(name):
+    """A workload at full size in the benchmark's launch configuration (its
+    own checkpoint format), design box widened to the whole lattice: a
     two-step window and its adjoint over the whole lattice, against the
-    oracle's on the 12 columns around the objective planes (x = 48).  In two
-    steps the adjoint of the plane's samples reaches two columns to each side,
-    so J, the gradient and the start-field adjoint of the columns away from the
-    cuts are those of the whole lattice."""
-    case = f32_inputs(I.WORKLOADS["ubend384x192x192"]()).replace(window_len=2, ckpt_every=2,
-                                                                design_box=(1, 383, 1, 191, 1, 191))
+    oracle's on 12-14 columns around each objective plane.  In two steps the
+    adjoint of a plane's samples reaches two columns to each side, so the
+    gradient and the start-field adjoint of the columns away from the cuts are
+    those of the whole lattice, J is the sum of the crops' (it is linear in
+    the plane weights), and the gradient is exactly zero beyond that reach.
+    The spin-up (5000 steps) brings flow to every plane: the sensitivity
+    -6 m.A1 vanishes where the fluid is still at rest.  The recompute starts
+    from the window's checkpoint, stored in the workload's format: a BF16
+    deviation keeps 8 significant bits (rounding 2^-9 of itself), FP16 11, so
+    the gradient bound is 5e-3 with BF16 and 1e-3 otherwise."""
+    case = f32_inputs(I.WORKLOADS[name]())
+    tol = 5e-3 if case.ckpt_format == I.CKPT_BF16 else 1e-3
     q, nx, ny, nz = case.lattice, case.nx, case.ny, case.nz
+    z0, z1 = (1, nz - 1) if q == 19 else (0, 1)
+    case = case.replace(window_len=2, ckpt_every=2, design_box=(1, nx - 1, 1, ny - 1, z0, z1))
     sol = B.Solver(case, B.LBM_FP32)
-    sol.advance(300)
+    sol.advance(5000)
     p0 = sol.get_state().reshape(q, nz, ny, nx)
     J, _ = sol.step_window()
     sol.adjoint_window()
     grad = sol.design_gradient().reshape(nz, ny, nx)
     a0 = sol.get_adjoint_state().reshape(q, nz, ny, nx)
     sol.close()
-    x0, x1 = 42, 54
-    crop = _x_crop(case, x0, x1)
-    pr = O.Problem(crop)
-    _, Jw, _, traj = pr.run_window(p0[:, :, :, x0:x1].reshape(q, -1))
-    _, grad_w, a0_w = pr.adjoint_window(traj)
-    assert abs(J - Jw) <= 1e-4 * abs(Jw)
-    g, gw = grad[:, :, x0 + 1:x1 - 1], grad_w.reshape(nz, ny, x1 - x0)[:, :, 1:-1]
-    a, aw = a0[:, :, :, x0 + 1:x1 - 1], a0_w.reshape(q, nz, ny, x1 - x0)[:, :, :, 1:-1]
-    assert np.count_nonzero(gw) > 0 and np.count_nonzero(aw) > 0
-    assert cosine(g, gw) > 0.9999 and rel_err(g, gw) < 1e-3
-    assert cosine(a, aw) > 0.9999 and rel_err(a, aw) < 1e-3
-    assert np.all(grad[:, :, :x0 + 2] == 0) and np.all(grad[:, :, x1 - 2:] == 0)   # beyond the adjoint's reach
+    J_crops = 0.0
+    reach = np.zeros(nx, bool)
+    for x0, x1 in FULL_SIZE_ADJOINT_CROPS[name]:
+        crop = _x_crop(case, x0, x1)
+        pr = O.Problem(crop)
+        _, Jw, _, traj = pr.run_window(p0[:, :, :, x0:x1].reshape(q, -1))
+        _, grad_w, a0_w = pr.adjoint_window(traj)
+        J_crops += Jw
+        lo, hi = (1 if x0 > 0 else 0), (x1 - x0 - 1 if x1 < nx else x1 - x0)
+        g, gw = grad[:, :, x0 + lo:x0 + hi], grad_w.reshape(nz, ny, x1 - x0)[:, :, lo:hi]
+        a, aw = a0[:, :, :, x0 + lo:x0 + hi], a0_w.reshape(q, nz, ny, x1 - x0)[:, :, :, lo:hi]
+        assert np.count_nonzero(gw) > 0 and np.count_nonzero(aw) > 0
+        assert cosine(g, gw) > 0.9999 and rel_err(g, gw) < tol, (x0, x1, cosine(g, gw), rel_err(g, gw))
+        assert cosine(a, aw) > 0.9999 and rel_err(a, aw) < tol, (x0, x1, cosine(a, aw), rel_err(a, aw))
+        reach[x0 + 2:x1 - 2] = True
+    assert abs(J - J_crops) <= 1e-4 * abs(J_crops)
+    assert np.all(grad[:, :, ~reach] == 0)
 
 
 def test_channel_workload_fp64_at_full_size_against_oracle():

@@ -118,6 +118,14 @@ ADJ_CASES = {
     # pressure drop between the legs at x = 8: a 12-step adjoint reaches the
     # transposed inlet and zero-gradient rules on the x = 0 face; the design
     # box spans the whole duct so that the gradient sees them
+    # the smallest bounded lattices (one interior node) and a single inner row
+    # with a ragged tail
+    "smallest-2d-3x3": lambda: I.small_channel(3, 3, obj_kind=I.OBJ_DISSIPATION, window_len=6, ckpt_every=2,
+                                               tau=0.56),
+    "smallest-3d-3x3x3": lambda: I.small_duct3d(3, 3, 3, obj_kind=I.OBJ_DISSIPATION, window_len=6, ckpt_every=2,
+                                                tau=0.56),
+    "one-inner-row-130x3": lambda: I.small_channel(130, 3, outlet=I.OUTLET_ZG, obj_kind=I.OBJ_VELOCITY_DEV,
+                                                   window_len=8, ckpt_every=4, tau=0.53),
     "ubend48x28x16-pressure": lambda: I.ubend_case(48, 28, 16, 8, tau=0.52, cs_smag=0.1, window_len=12,
                                                    ckpt_every=4, ckpt_format=I.CKPT_NATIVE).replace(
                                                        design_box=(1, 47, 1, 27, 1, 15)),
@@ -170,6 +178,51 @@ def test_window_and_adjoint_fp32_match_oracle(name):
     assert cosine(grad[m], grad_w[m]) > 0.9999
     assert rel_err(grad[m], grad_w[m]) < 1e-3
     assert cosine(a0, a0_w) > 0.9999
+
+
+# Windows whose only sample is taken on f^{n0}, pulled from the fixed start
+# field: |W| = 1, and dW = |W|.
+DESIGN_FREE_WINDOWS = {
+    "single-step-window": lambda: I.small_channel(133, 10, obj_kind=I.OBJ_PRESSURE, window_len=1, ckpt_every=1,
+                                                  tau=0.56),
+    "one-sample-per-window": lambda: I.small_duct3d(131, 6, 6, window_len=6, sample_every=6, ckpt_every=3,
+                                                    tau=0.53),
+}
+
+
+@pytest.mark.parametrize("name", list(DESIGN_FREE_WINDOWS))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_windows_whose_sample_precedes_the_design(name, precision):
+    """The window's only sample is taken on the field pulled from the fixed
+    start field (Eq. 42 with samples at n0, n0 + dW, ...), so J does not
+    depend on the design: the oracle's gradient and the GPU's are exactly
+    zero, and the start-field adjoint is the sample's own source."""
+    case = f32_inputs(DESIGN_FREE_WINDOWS[name]())
+    pr = O.Problem(case)
+    p0 = _developed(pr, 40)
+    _, Jw, _, traj = pr.run_window(p0)
+    _, grad_w, a0_w = pr.adjoint_window(traj)
+    assert np.all(grad_w == 0) and np.count_nonzero(a0_w) > 0
+    prec = B.LBM_FP64 if precision == "fp64" else B.LBM_FP32
+    _, J, _, Jeff, grad, a0 = _gpu_window_and_adjoint(case, prec, p0)
+    assert np.all(grad == 0)
+    assert abs(J - Jw) <= (1e-12 if precision == "fp64" else 1e-5) * abs(Jw)
+    assert rel_err(a0, a0_w) < (1e-11 if precision == "fp64" else 1e-5)
+
+
+def test_zero_objective_weights():
+    """No objective weights: J is exactly 0, the adjoint sweep carries exact
+    zeros (start-field adjoint and gradient), and the window's monitor is the
+    oracle's."""
+    case = f32_inputs(I.small_duct3d(131, 6, 5, window_len=8, ckpt_every=4, tau=0.53))
+    case = case.replace(obj_weights=np.zeros_like(case.obj_weights))
+    pr = O.Problem(case)
+    p0 = _developed(pr, 30)
+    _, Jw, Mw, _ = pr.run_window(p0)
+    _, J, M, Jeff, grad, a0 = _gpu_window_and_adjoint(case, B.LBM_FP64, p0)
+    assert Jw == 0 and J == 0 and Jeff == 0
+    assert np.all(grad == 0) and np.all(a0 == 0)
+    assert abs(M - Mw) <= 1e-12 * abs(Mw)
 
 
 def test_recompute_from_checkpoints_is_bitwise():

@@ -225,6 +225,21 @@ def test_zero_objective_weights():
     assert abs(M - Mw) <= 1e-12 * abs(Mw)
 
 
+def test_empty_design_box():
+    """An empty design box: the gradient is exactly zero everywhere, while J,
+    the monitor and the start-field adjoint are the oracle's."""
+    case = f32_inputs(I.small_channel(140, 11, obj_kind=I.OBJ_VELOCITY_DEV, window_len=12, ckpt_every=4,
+                                      outlet=I.OUTLET_ZG, tau=0.52)).replace(design_box=(5, 5, 0, 0, 0, 0))
+    pr = O.Problem(case)
+    p0 = _developed(pr, 40)
+    _, Jw, Mw, traj = pr.run_window(p0)
+    _, _, a0_w = pr.adjoint_window(traj)
+    _, J, M, _, grad, a0 = _gpu_window_and_adjoint(case, B.LBM_FP64, p0)
+    assert np.all(grad == 0)
+    assert abs(J - Jw) <= 1e-12 * abs(Jw) and abs(M - Mw) <= 1e-12 * abs(Mw)
+    assert rel_err(a0, a0_w) < 1e-11
+
+
 def test_recompute_from_checkpoints_is_bitwise():
     """Segments of K < |W| recompute the same trajectory: the adjoint field is
     bitwise identical; the gradient differs only by the order in which the

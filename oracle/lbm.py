@@ -45,6 +45,12 @@ design notes):
 * D3Q19 (beyond the paper): same collision with p,q in {x,y,z}; velocity
   inlet by the linear moving-wall bounce-back f_a = f_abar + 2 w_a rho0 c_a.u/cs^2
   with rho0 = 1; zero-gradient outlet copies the neighbour along the inward normal.
+
+Pins: every function above is checked against closed forms, invariants, the
+paper's printed adjoint boundary coefficients, complex-step derivatives and
+finite differences (tests/test_oracle_*.py), with planted mistakes that must
+fail them.  Parity unpinned: the absolute values of J and C_d on the
+benchmark workloads' own geometries, for which the paper prints no values.
 """
 from __future__ import annotations
 

@@ -34,7 +34,13 @@ they are the standard safeguard of the method and zero whenever the
 approximated constraints can be met.  Readings where Svanberg 1987 leaves a
 choice (s0 = 0.5, s_slow = 0.7, s_fast = 1.2, a = 0.1, the [0.01, 10] bounds
 of the asymptote distance, c_i) are listed in the design notes.
-"""
+
+Pins (tests/test_oracle_mma.py): first-order agreement of the approximation
+with finite differences, the asymptote rules on hand-worked numbers, the
+subproblem's KKT conditions and an SLSQP solve of its primal, the closed-form
+optimum of min sum c/x under a volume bound, and planted mistakes that must
+fail them.
+
 from __future__ import annotations
 
 import numpy as np

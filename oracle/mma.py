@@ -40,6 +40,7 @@ with finite differences, the asymptote rules on hand-worked numbers, the
 subproblem's KKT conditions and an SLSQP solve of its primal, the closed-form
 optimum of min sum c/x under a volume bound, and planted mistakes that must
 fail them.
+"""
 
 from __future__ import annotations
 

@@ -159,6 +159,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def clocks_rejected(c):
+    """A clock record the timing rules reject: hw_slowdown, hw_thermal_slowdown
+    or sw_thermal_slowdown active, or a median SM clock below 85% of the
+    maximum with no reason active (sw_power_cap is kept and noted)."""
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(c.get("reasons", [])):
+        return True
+    sm, mx = c.get("sm_mhz"), c.get("sm_max_mhz")
+    return bool(sm and mx and sm < 0.85 * mx and not c.get("reasons"))
+
+
 # --------------------------------------------------------------- roofline --
 
 def bytes_per_lu(case, phase, rs=4):
@@ -582,18 +593,34 @@ def run_ours(args, case, rank, world, local):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    sol.get_timing()          # reset the phase counters
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xff)
-                ev[k][0].record(stream)
-                one_step(timed=True)
-                ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    def timed_pass():
+        """The timed region: K steps, the L2 flushed before each, CUDA events
+        on the library stream, nvidia-smi clocks sampled throughout."""
+        sol.get_timing()          # reset the phase counters
+        sweep_ev.clear()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(k & 0xff)
+                    ev[k][0].record(stream)
+                    one_step(timed=True)
+                    ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev), clk.summary()
+
+    ms, clocks = timed_pass()
+    # A pass that saw a hardware or thermal slowdown, or SM clocks far below
+    # their maximum with no reason given (a leftover clock lock), is measured
+    # once more; every rank takes part if any rank saw one.
+    if reduce_max(float(clocks_rejected(clocks)), world) > 0:
+        first = clocks
+        if world > 1:
+            dist.barrier()
+        ms, clocks = timed_pass()
+        clocks["remeasured_after"] = first
     timing = sol.get_timing()
     sched = sol.schedule()
     ms = reduce_max(ms, world)
@@ -686,7 +713,6 @@ def run_ours(args, case, rank, world, local):
                                    "design_bytes_per_lu": sweep_b / n, "gbs_design_count": sweep_b / (sweep_us / 1e6) / 1e9,
                                    "frac_design_count": sweep_b / (sweep_us / 1e6) / 1e9 / hbm},
             "phases": phase_rows}
-    clocks = clk.summary()
     if rs == 8:
         for v in kernels.values():
             v["case"] = case

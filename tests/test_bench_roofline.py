@@ -79,3 +79,17 @@ def test_committed_fp64_counts_cover_both_stencils(bench):
         n = e["nodes"]
         assert e["inst_per_lu"] == pytest.approx((e["dadd"] + e["dmul"] + e["dfma"]) / n)
         assert e["flop_per_lu"] == pytest.approx((e["dadd"] + e["dmul"] + 2 * e["dfma"]) / n)
+
+
+def test_clock_records_the_timing_rules_reject(bench):
+    """Rejected: a hardware or thermal slowdown, or SM clocks far below their
+    maximum with no reason (a leftover lock); kept: a power cap, full clocks,
+    or no samples at all."""
+    rej = bench.clocks_rejected
+    assert rej({"sm_mhz": 2032.0, "sm_max_mhz": 2032.0, "reasons": ["hw_slowdown"]})
+    assert rej({"sm_mhz": 1900.0, "sm_max_mhz": 2032.0, "reasons": ["sw_thermal_slowdown", "sw_power_cap"]})
+    assert rej({"sm_mhz": 1200.0, "sm_max_mhz": 2032.0, "reasons": []})
+    assert not rej({"sm_mhz": 1200.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"]})
+    assert not rej({"sm_mhz": 1942.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"]})
+    assert not rej({"sm_mhz": 2032.0, "sm_max_mhz": 2032.0, "reasons": []})
+    assert not rej({"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0})
